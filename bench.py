@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark of the B300 page cipher (MemShield Sec. 4.4 hot path).
+
+Default workload (one JSON line on rank 0): the bulk device-resident
+configuration -- 1 GiB = 262,144 pages x 4 KiB of SplitMix64(seed 2) bytes in
+HBM, page ids 0..262143, key = SplitMix64(seed 1)[0:32].  One step is one
+encrypt launch plus one decrypt launch over the whole buffer, through the
+C-ABI device-list entry points.  The buffer (1 GiB) is larger than the L2
+(126 MB), so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``value`` is page bytes processed per second (encrypt and decrypt bytes both
+count) over all ranks; ``e2e`` is the same metric through ms_crypt_host with
+the pages in pinned HOST memory (host<->device copies inside the timed
+region); ``roofline`` relates the page kernel's average launch time to the
+integer-ALU peak; ``cpu_baseline`` times the CPU oracle on the host cores on
+a bounded sample of the same buffer.  Under torchrun (N > 1) every rank runs
+an independent replica on its own GPU (the pages shard with no exchange).
+``--impl reference`` times the CPU oracle itself on this workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PAGE = 4096
+BULK_PAGES = 262144
+OPS_PER_BLOCK = 992            # 80 quarter rounds x 12 + 16 feed-forward adds + 16 data XORs
+INT32_LANES_PER_SM = 128       # 4 schedulers x 32 lanes issue one int32 op each per clock
+WORKLOAD = ("bulk: 1 GiB = 262,144 x 4 KiB pages resident in HBM (SplitMix64 seed 2), page ids "
+            "0..262143, key = SplitMix64(seed 1)[0:32], ChaCha20; one encrypt launch + one decrypt "
+            "launch per step")
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2004_09252_b300", "csrc", "ms_cipher.cuh"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the bulk page kernel from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "k_pages_bulk_1gib.md")
+    if not os.path.exists(p):
+        return None
+    text = open(p).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.e+]+)", text)
+    h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1))
+
+
+# ------------------------------------------------------------------ clocks
+REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+           0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown", 0x2: "applications_clocks_setting",
+           0x1: "gpu_idle", 0x10: "sync_boost"}
+
+
+class ClockSampler:
+    """Samples SM clock and clock-event reasons with NVML while the timed region runs."""
+
+    def __init__(self, torch_dev: int, period_s: float = 0.02):
+        self.samples, self.reasons, self.max_mhz = [], set(), None
+        self.period = period_s
+        self._stop = threading.Event()
+        self._t = None
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            import torch
+            props = torch.cuda.get_device_properties(torch_dev)
+            h = None
+            try:
+                bus = "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+                h = pynvml.nvmlDeviceGetHandleByPciBusId(bus)
+            except Exception:
+                h = pynvml.nvmlDeviceGetHandleByIndex(torch_dev)
+            self.nvml, self.h = pynvml, h
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
+        except Exception as e:  # no NVML: report the absence
+            self.nvml, self.h, self.err = None, None, str(e)
+
+    def _run(self):
+        n = self.nvml
+        while not self._stop.is_set():
+            try:
+                self.samples.append(n.nvmlDeviceGetClockInfo(self.h, n.NVML_CLOCK_SM))
+                try:
+                    r = n.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                except AttributeError:
+                    r = n.nvmlDeviceGetCurrentClocksThrottleReasons(self.h)
+                for bit, name in REASONS.items():
+                    if r & bit and name != "gpu_idle":
+                        self.reasons.add(name)
+            except Exception:
+                pass
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.nvml:
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._t:
+            self._t.join()
+
+    def summary(self):
+        if not self.nvml:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": "NVML unavailable"}
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
+                "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons), "samples": len(self.samples)}
+
+
+# --------------------------------------------------------------- CPU oracle
+def cpu_oracle_rate(seconds: float, threads: int):
+    """Time the CPU oracle (as it stands) on a bounded sample of the bulk buffer."""
+    import numpy as np
+
+    import oracle
+    import synth
+    oracle.build()
+    key = synth.key_bytes(1)
+    cal = synth.page_bytes_fast(2, 0, 32)
+    ids = np.arange(32, dtype=np.uint64)
+    t0 = time.perf_counter()
+    oracle.crypt_pages(key, cal, ids, ids, threads=1)
+    per_page = (time.perf_counter() - t0) / 32
+    n = int(max(threads * 8, min(BULK_PAGES, seconds / per_page * threads)))
+    buf = synth.page_bytes_fast(2, 0, n)
+    ids = np.arange(n, dtype=np.uint64)
+    t0 = time.perf_counter()
+    oracle.crypt_pages(key, buf, ids, ids, threads=threads)
+    dt = time.perf_counter() - t0
+    return n * PAGE / dt / 1e9, n, dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2004_09252_b300 import memshield as ms
+
+    rank, world, local = env_rank()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    key = synth.key_bytes(1)
+    n = args.pages
+    plain = synth.page_bytes_fast(2, 0, n)
+    d = torch.from_numpy(plain).to(f"cuda:{dev}")
+    ids = np.arange(n, dtype=np.uint64)
+    lst = torch.from_numpy(ms.pages_array(d.data_ptr() + PAGE * ids, ids).view(np.uint8)).to(f"cuda:{dev}")
+    ctx = ms.Context(key, device=dev, stream=stream.cuda_stream)
+    if args.shape:
+        b, t, u, p = (int(x) for x in args.shape.split(","))
+        ctx.set_shape(b, t, u, p)
+    shape = ctx.get_shape()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ctx.encrypt_pages_dev(lst, n)
+        ctx.decrypt_pages_dev(lst, n)
+    if ctx.sync() != 0:
+        raise RuntimeError("warm-up failed")
+    # correctness guard: after warm-up (even number of XORs) the buffer is the plaintext
+    if not torch.equal(d[:PAGE * 64], torch.from_numpy(plain[:PAGE * 64]).to(d.device)):
+        raise RuntimeError("round trip check failed")
+
+    K = args.steps
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K + 1)]
+    sampler = ClockSampler(dev)
+    barrier()
+    with sampler:
+        evs[0].record(stream)
+        for k in range(K):
+            ctx.encrypt_pages_dev(lst, n)
+            evs[2 * k + 1].record(stream)
+            ctx.decrypt_pages_dev(lst, n)
+            evs[2 * k + 2].record(stream)
+        barrier()
+    rc = ctx.sync()
+    if rc != 0:
+        raise RuntimeError(f"ms_sync failed: {ms.strerror(rc)}")
+    launch_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(2 * K)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    t = torch.tensor([total_ms], dtype=torch.float64, device=d.device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    bytes_all = 2.0 * K * n * PAGE * world
+    value = bytes_all / (total_ms / 1e3) / 1e9
+    avg_launch_s = statistics.mean(launch_ms) / 1e3
+
+    peaks, peaks_kind = load_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    alu_peak = props.multi_processor_count * INT32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    ops_launch = n * 64 * OPS_PER_BLOCK
+    achieved = ops_launch / avg_launch_s / 1e12
+    alg_bytes = n * (2 * PAGE + 16)
+    traffic = profiled_traffic()
+
+    # e2e through the host-page entry point (pinned host memory, copies timed)
+    e2e = None
+    if not args.no_e2e:
+        hbuf = torch.empty(n * PAGE, dtype=torch.uint8).pin_memory()
+        synth.fill_pages(hbuf.data_ptr(), 2, 0, n)
+        chunk = args.e2e_chunk_mib << 20
+        ctx.crypt_host(ms.MS_ENCRYPT, hbuf, 0, n, chunk, args.e2e_streams)
+        ctx.crypt_host(ms.MS_DECRYPT, hbuf, 0, n, chunk, args.e2e_streams)
+        es = max(2, min(5, K))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(es):
+            ctx.crypt_host(ms.MS_ENCRYPT, hbuf, 0, n, chunk, args.e2e_streams)
+            ctx.crypt_host(ms.MS_DECRYPT, hbuf, 0, n, chunk, args.e2e_streams)
+        barrier()
+        el = time.perf_counter() - t0
+        te = torch.tensor([el], dtype=torch.float64, device=d.device)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        el = float(te.item())
+        ok = np.array_equal(hbuf[:PAGE * 16].numpy(), plain[:PAGE * 16])
+        e2e = {"value": round(2.0 * es * n * PAGE * world / el / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": 2 * n * PAGE, "d2h_bytes_per_step": 2 * n * PAGE,
+               "steps": es, "chunk_bytes": chunk, "streams": args.e2e_streams or 2,
+               "host_memory": "pinned", "round_trip_ok": bool(ok)}
+        del hbuf
+
+    ctx.shutdown()
+    line = {
+        "metric": "page encrypt GB/s (ChaCha20, 4 KiB pages, device-resident)",
+        "value": round(value, 3),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(total_ms / K, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic (SplitMix64 seeded page bytes)",
+        "config": {"workload": WORKLOAD if n == BULK_PAGES else f"profiling case: {n} pages of the bulk buffer",
+                   "pages": n, "page_bytes": PAGE, "rounds": 20,
+                   "l2": "inputs larger than L2 (1 GiB vs 126 MB), no flush", "parallelism": f"replicas{world}",
+                   "shape": shape},
+        "gpu_launches": 2 * K,
+        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 3),
+                     "unit": "Tops/s (int32)", "frac": round(achieved / alu_peak, 4), "traffic": traffic,
+                     "peak_source": f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} int32 lanes x "
+                                    f"{sm_max:.0f} MHz ({peaks_kind} max SM clock)",
+                     "ops_per_launch": ops_launch, "avg_launch_ms": round(avg_launch_s * 1e3, 5),
+                     "hbm": {"achieved_gbs": round(alg_bytes / avg_launch_s / 1e9, 1),
+                             "peak_gbs": peaks.get("hbm_gbs"),
+                             "frac": round(alg_bytes / avg_launch_s / 1e9 / float(peaks.get("hbm_gbs", 6400.0)), 4),
+                             "note": f"{peaks_kind} copy bandwidth"}},
+        "clocks": sampler.summary(),
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        threads = host_cores()
+        v, npg, dt = cpu_oracle_rate(args.cpu_seconds, threads)
+        line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                                "sample": f"{npg} pages ({npg * PAGE / 2**20:.0f} MiB) of the bulk buffer, "
+                                          f"one encrypt pass, {dt:.1f} s, pages split over {threads} threads"}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- reference
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    import synth
+    oracle.build()
+    threads = host_cores()
+    key = synth.key_bytes(1)
+    cal = synth.page_bytes_fast(2, 0, 32)
+    ids = np.arange(32, dtype=np.uint64)
+    t0 = time.perf_counter()
+    oracle.crypt_pages(key, cal, ids, ids, threads=1)
+    per_page = (time.perf_counter() - t0) / 32
+    budget = min(150.0, max(20.0, 1.5 * (args.steps + args.warmup)))
+    step_s = budget / (args.steps + args.warmup)
+    npg = int(max(threads * 4, min(BULK_PAGES, step_s / per_page * threads / 2)))
+    buf = synth.page_bytes_fast(2, 0, npg)
+    ids = np.arange(npg, dtype=np.uint64)
+    for _ in range(args.warmup):
+        oracle.crypt_pages(key, buf, ids, ids, threads=threads)
+        oracle.crypt_pages(key, buf, ids, ids, threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.crypt_pages(key, buf, ids, ids, threads=threads)
+        oracle.crypt_pages(key, buf, ids, ids, threads=threads)
+    dt = time.perf_counter() - t0
+    value = 2.0 * args.steps * npg * PAGE / dt / 1e9
+    sample = (f"each step: encrypt + decrypt of the first {npg} pages ({npg * PAGE / 2**20:.1f} MiB) of the "
+              f"bulk buffer on {threads} threads")
+    print(json.dumps({
+        "impl": "reference", "metric": "page encrypt GB/s (ChaCha20, 4 KiB pages, device-resident)",
+        "value": round(value, 4), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic (SplitMix64 seeded page bytes)",
+        "config": {"workload": WORKLOAD, "pages": BULK_PAGES, "page_bytes": PAGE, "rounds": 20,
+                   "l2": "host memory", "parallelism": "cpu"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--pages", type=int, default=BULK_PAGES,
+                    help="pages in the buffer (default: the 1 GiB bulk workload; smaller only for profiling)")
+    ap.add_argument("--shape", default="", help="K1 shape override: bpt,tpc,unroll,rot_policy")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--e2e-chunk-mib", type=int, default=16)
+    ap.add_argument("--e2e-streams", type=int, default=2)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * memshield.h -- C ABI of the B300 page cipher (MemShield, arXiv 2004.09252).
+ *
+ * What the library computes (MemShield Sec. 4.4, "GPU encryption"): every
+ * operation acts on whole 4096-byte pages.  A page is XORed, in place, with
+ * 64 ChaCha20 keystream blocks of 64 bytes.  Each block is derived from the
+ * 256-bit master key and a 128-bit value made of the page's identity, the
+ * client identity (PID) and the block's index 0..63 inside the page.
+ * Encryption and decryption are the same operation.
+ *
+ * Field layout of the 128-bit value (the paper gives no order; this is the
+ * library's fixed reading, in the RFC 8439 ChaCha20 state layout):
+ *   word 12 = block index j (0..63), word 13 = low 32 bits of the page id,
+ *   word 14 = high 32 bits of the page id, word 15 = the domain word (the
+ *   paper's PID slot; ms_config.domain, 0 by default).
+ * The round count is 20 (the paper's ChaCha20); 8 and 12 are accepted as
+ * reduced-round variants.
+ *
+ * Memory: page addresses are device-accessible pointers (device memory, or
+ * pinned host memory mapped into the device's address space), each 16-byte
+ * aligned.  The caller owns page memory and must keep it valid and untouched
+ * until ms_sync() returns for the submission.  A page must not appear twice in
+ * one submission (two in-place updates of one page would race); re-encrypting
+ * a page with the same (key, page id, domain) reuses its keystream, as in the
+ * paper, which keeps no per-page version.
+ *
+ * Key: ms_init copies the key into device memory through a pinned bounce
+ * buffer that it wipes before returning; afterwards the library holds the key
+ * only on the device (the paper keeps it in the registers of a kernel that
+ * never exits, Sec. 4.4; this library keeps it in a device buffer instead, so
+ * launches can end).  Copies made by the CUDA driver itself are outside the
+ * library's control.
+ *
+ * Errors: every int-returning call returns MS_OK (0) or a negative MS_E* code;
+ * ms_strerror() names it.  n = 0 is a successful no-op.  Calls on one context
+ * may come from several host threads; submissions are serialised internally.
+ */
+#ifndef MEMSHIELD_H
+#define MEMSHIELD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MS_PAGE_BYTES 4096u
+#define MS_BLOCK_BYTES 64u
+#define MS_BLOCKS_PER_PAGE 64u
+#define MS_KEY_BYTES 32u
+
+enum ms_status {
+  MS_OK = 0,
+  MS_EINVAL = -1,     /* bad argument: NULL, misaligned page, bad op/rounds/size */
+  MS_ENOTINIT = -2,   /* NULL or shut-down context */
+  MS_ENOMEM = -3,     /* host or device allocation failed */
+  MS_ECUDA = -4,      /* a CUDA runtime call failed (ms_last_cuda_error gives the code) */
+  MS_ETIMEDOUT = -5,  /* a bounded wait ran out; the work may still complete later */
+  MS_EBUSY = -6,      /* admission refused: queue or staging budget full */
+  MS_ERANGE = -7      /* size beyond a stated maximum */
+};
+
+enum ms_op { MS_ENCRYPT = 0, MS_DECRYPT = 1 };
+
+/* One page of a submission: where the bytes live and which id seeds its nonce. */
+typedef struct ms_page {
+  uint64_t addr;    /* device-accessible address of the 4096-byte page, 16-byte aligned */
+  uint64_t page_id; /* nonce words 13..14 (the paper's page address) */
+} ms_page;
+
+typedef struct ms_ctx ms_ctx;
+
+typedef struct ms_config {
+  int device;                  /* CUDA device ordinal; -1 = the calling thread's current device */
+  void *stream;                /* cudaStream_t to launch on; NULL = a stream the library creates */
+  uint32_t domain;             /* nonce word 15 (the paper's client PID); default 0 */
+  uint32_t rounds;             /* 20 (default), or 8 / 12 */
+  uint32_t list_capacity;      /* entries per host-list staging slot (default 65536) */
+  uint32_t timeout_ms;         /* bound on every host-side wait (default 10000) */
+  uint32_t blocks_per_thread;  /* 0 = tuned default; else 1, 2 or 4 keystream blocks per thread */
+  uint32_t threads_per_cta;    /* 0 = tuned default; else 128, 256 or 512 */
+  uint32_t dr_unroll;          /* 0 = tuned default; else double rounds per loop trip: 1, 2 or rounds/2 */
+  uint32_t check_duplicates;   /* nonzero: host-list calls reject a page address listed twice */
+} ms_config;
+
+/* Fill *cfg with the defaults listed above. */
+void ms_config_default(ms_config *cfg);
+
+/*
+ * Create a context on cfg->device: copy the 32-byte master key to device
+ * memory (key == NULL draws it from the OS CSPRNG, getrandom(2), as the paper
+ * does, Sec. 4.4), create the stream and the staging buffers.  *out receives
+ * the context; on failure *out is NULL and nothing is left allocated.
+ */
+int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg);
+
+/*
+ * Encrypt / decrypt (the same transform, Sec. 4.4) n pages listed in HOST
+ * memory.  Every entry is checked first (addr != 0, addr % 16 == 0); one bad
+ * entry fails the whole call with MS_EINVAL and launches nothing.  The list is
+ * copied before the call returns (the caller may reuse it at once); the work
+ * is queued on the context's stream and completes asynchronously: ms_sync()
+ * waits for it.
+ */
+int ms_encrypt_pages(ms_ctx *ctx, const ms_page *pages, size_t n);
+int ms_decrypt_pages(ms_ctx *ctx, const ms_page *pages, size_t n);
+
+/*
+ * Same, with the entry list already in DEVICE memory (d_pages, 16-byte
+ * aligned, owned by the caller, valid until ms_sync returns).  Entries are
+ * checked on the device: a bad entry is skipped and the next ms_sync returns
+ * MS_EINVAL; the good entries are still processed.
+ */
+int ms_encrypt_pages_dev(ms_ctx *ctx, const ms_page *d_pages, size_t n);
+int ms_decrypt_pages_dev(ms_ctx *ctx, const ms_page *d_pages, size_t n);
+
+/*
+ * Contiguous form: n_pages pages back to back at the device address d_base
+ * (16-byte aligned); page k has id first_page_id + k.  No entry list is read.
+ */
+int ms_crypt_range(ms_ctx *ctx, int op, void *d_base, uint64_t first_page_id, size_t n_pages);
+
+/*
+ * Wait, at most cfg.timeout_ms, until all work submitted on this context has
+ * finished.  Returns MS_ETIMEDOUT if the bound ran out (the work is still
+ * queued; call again), MS_EINVAL if a device-checked entry was bad since the
+ * last ms_sync, MS_ECUDA on a CUDA error.
+ */
+int ms_sync(ms_ctx *ctx);
+
+/*
+ * Finish outstanding work (bounded), overwrite the device key with zeros and
+ * free every resource.  ctx must not be used afterwards.  NULL is a no-op.
+ */
+int ms_shutdown(ms_ctx *ctx);
+
+/*
+ * Launch shape of the page kernels (what the autotuner picks).  Not part of
+ * the method: every shape computes the same bytes.
+ *   blocks_per_thread  1, 2 or 4 keystream blocks per thread
+ *   threads_per_cta    128, 256 or 512
+ *   dr_unroll          double rounds per loop trip (1, 2, or all of them)
+ *   rot_policy         0: rotations as funnel shifts; 1: rotations by 16 and 8
+ *                      as byte permutes; 2: as 1, with 12 and 7 done on the
+ *                      integer multiply pipe (x * 2^k, high + low halves)
+ * ms_set_shape returns MS_EINVAL (and changes nothing) for a shape that is
+ * not compiled for the context's round count.
+ */
+typedef struct ms_shape {
+  uint32_t blocks_per_thread;
+  uint32_t threads_per_cta;
+  uint32_t dr_unroll;
+  uint32_t rot_policy;
+} ms_shape;
+
+int ms_get_shape(const ms_ctx *ctx, ms_shape *out);
+int ms_set_shape(ms_ctx *ctx, const ms_shape *shape);
+
+/* Static English description of an ms_status code. */
+const char *ms_strerror(int code);
+
+/* The cudaError_t of the most recent MS_ECUDA on this context (0 if none). */
+int ms_last_cuda_error(const ms_ctx *ctx);
+
+/*
+ * Host pages, streamed (end-to-end form).  n_pages pages back to back at the
+ * HOST address host_base (pinned memory gives overlapped copies; pageable
+ * memory works but serialises); page k has id first_page_id + k.  The range
+ * is cut into chunks of chunk_bytes (a multiple of 4096, 0 = 16 MiB); chunk i
+ * goes host->device, through the cipher and back on stream i % n_streams
+ * (n_streams 1..4, 0 = 2) with its own device buffer, so copies in both
+ * directions overlap the kernels.  Returns when the results are back in
+ * host memory (bounded by timeout_ms per chunk).
+ */
+int ms_crypt_host(ms_ctx *ctx, int op, void *host_base, uint64_t first_page_id, size_t n_pages,
+                  size_t chunk_bytes, int n_streams);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MEMSHIELD_H */

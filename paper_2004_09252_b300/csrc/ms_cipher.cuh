@@ -1,0 +1,193 @@
+// Device side of the page cipher: the ChaCha20 block held in registers and the
+// page kernels built on it.
+//
+// Method (MemShield Sec. 4.4): a 4096-byte page is XORed in place with the 64
+// keystream blocks whose 128-bit seed value is (block index j = 0..63, page
+// id, domain); the 256-bit key sits in device memory.  Each thread makes one
+// 64-byte keystream block at a time and XORs it into the same 64 bytes of the
+// page, so a block never leaves the thread's registers.  ChaCha20 block: the
+// 16-word state (four constant words, eight key words, the counter, three
+// nonce words) goes through 10 double rounds, each four column
+// quarter-rounds and four diagonal quarter-rounds, and the input state is
+// then added back word by word.
+#pragma once
+
+#include <cstdint>
+
+#include "memshield.h"
+
+namespace ms {
+
+// ASCII "expand 32-byte k" as four little-endian 32-bit words.
+constexpr uint32_t kSigma0 = 0x61707865u;  // "expa"
+constexpr uint32_t kSigma1 = 0x3320646eu;  // "nd 3"
+constexpr uint32_t kSigma2 = 0x79622d32u;  // "2-by"
+constexpr uint32_t kSigma3 = 0x6b206574u;  // "te k"
+
+constexpr unsigned kStatusBadEntry = 1u;   // a device-side entry check failed
+
+// Rotation policies.  All compute the same left rotation; they differ in the
+// execution pipe the instruction lands on.
+//   kRotFunnel: every rotation is a funnel shift.
+//   kRotPerm:   rotations by 16 and 8 are byte permutes, 12 and 7 funnel shifts.
+//   kRotMul:    16 and 8 byte permutes; 12 and 7 as hi/lo halves of a 32x32
+//               multiply by 2^k (the multiplier comes from a kernel argument so
+//               it stays a real multiply) -- this moves work to the multiply pipe.
+enum RotPolicy { kRotFunnel = 0, kRotPerm = 1, kRotMul = 2 };
+
+struct MulConsts {
+  uint32_t m12;  // 1 << 12
+  uint32_t m7;   // 1 << 7
+};
+
+template <int N>
+__device__ __forceinline__ uint32_t rotl_funnel(uint32_t x) {
+  return __funnelshift_l(x, x, N);
+}
+
+template <int POL>
+__device__ __forceinline__ uint32_t rotl16(uint32_t x) {
+  if (POL == kRotFunnel) return rotl_funnel<16>(x);
+  return __byte_perm(x, 0u, 0x1032u);
+}
+
+template <int POL>
+__device__ __forceinline__ uint32_t rotl8(uint32_t x) {
+  if (POL == kRotFunnel) return rotl_funnel<8>(x);
+  return __byte_perm(x, 0u, 0x2103u);
+}
+
+// x * 2^k as a 64-bit product: low word = x << k, high word = x >> (32 - k);
+// the two never overlap, so their sum is the rotation.
+__device__ __forceinline__ uint32_t rotl_mul(uint32_t x, uint32_t m) {
+  uint32_t hi = __umulhi(x, m);
+  uint32_t r;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(m), "r"(hi));
+  return r;
+}
+
+template <int POL>
+__device__ __forceinline__ uint32_t rotl12(uint32_t x, const MulConsts &mc) {
+  if (POL == kRotMul) return rotl_mul(x, mc.m12);
+  return rotl_funnel<12>(x);
+}
+
+template <int POL>
+__device__ __forceinline__ uint32_t rotl7(uint32_t x, const MulConsts &mc) {
+  if (POL == kRotMul) return rotl_mul(x, mc.m7);
+  return rotl_funnel<7>(x);
+}
+
+template <int POL>
+__device__ __forceinline__ void quarter_round(uint32_t &a, uint32_t &b, uint32_t &c, uint32_t &d,
+                                              const MulConsts &mc) {
+  a += b; d = rotl16<POL>(d ^ a);
+  c += d; b = rotl12<POL>(b ^ c, mc);
+  a += b; d = rotl8<POL>(d ^ a);
+  c += d; b = rotl7<POL>(b ^ c, mc);
+}
+
+// Key words 0..7 and the per-page nonce words (13, 14, 15).
+struct BlockSeed {
+  uint32_t k[8];
+  uint32_t n0, n1, n2;
+};
+
+__device__ __forceinline__ void load_key(const uint4 *__restrict__ key, uint32_t (&k)[8]) {
+  const uint4 a = __ldg(key), b = __ldg(key + 1);
+  k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w;
+  k[4] = b.x; k[5] = b.y; k[6] = b.z; k[7] = b.w;
+}
+
+// Keystream block `counter` for `seed`, XORed into the 64 bytes at dst.
+// ROUNDS is 8, 12 or 20; UNR is how many double rounds one loop trip holds.
+template <int ROUNDS, int UNR, int POL>
+__device__ __forceinline__ void xor_block(uint4 *__restrict__ dst, const BlockSeed &s,
+                                          uint32_t counter, const MulConsts &mc) {
+  // Issue the page loads first so their latency hides behind the rounds.
+  uint4 d0 = __ldcs(dst + 0), d1 = __ldcs(dst + 1), d2 = __ldcs(dst + 2), d3 = __ldcs(dst + 3);
+
+  uint32_t x0 = kSigma0, x1 = kSigma1, x2 = kSigma2, x3 = kSigma3;
+  uint32_t x4 = s.k[0], x5 = s.k[1], x6 = s.k[2], x7 = s.k[3];
+  uint32_t x8 = s.k[4], x9 = s.k[5], x10 = s.k[6], x11 = s.k[7];
+  uint32_t x12 = counter, x13 = s.n0, x14 = s.n1, x15 = s.n2;
+
+  static_assert((ROUNDS / 2) % UNR == 0, "unroll must divide the double-round count");
+#pragma unroll 1
+  for (int r = 0; r < ROUNDS / 2; r += UNR) {
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      // column round
+      quarter_round<POL>(x0, x4, x8, x12, mc);
+      quarter_round<POL>(x1, x5, x9, x13, mc);
+      quarter_round<POL>(x2, x6, x10, x14, mc);
+      quarter_round<POL>(x3, x7, x11, x15, mc);
+      // diagonal round
+      quarter_round<POL>(x0, x5, x10, x15, mc);
+      quarter_round<POL>(x1, x6, x11, x12, mc);
+      quarter_round<POL>(x2, x7, x8, x13, mc);
+      quarter_round<POL>(x3, x4, x9, x14, mc);
+    }
+  }
+
+  // Feed-forward (add the input state), then XOR; words are little-endian in
+  // memory, which is the byte order of the uint4 lanes on the GPU.
+  d0.x ^= x0 + kSigma0;  d0.y ^= x1 + kSigma1;  d0.z ^= x2 + kSigma2;  d0.w ^= x3 + kSigma3;
+  d1.x ^= x4 + s.k[0];   d1.y ^= x5 + s.k[1];   d1.z ^= x6 + s.k[2];   d1.w ^= x7 + s.k[3];
+  d2.x ^= x8 + s.k[4];   d2.y ^= x9 + s.k[5];   d2.z ^= x10 + s.k[6];  d2.w ^= x11 + s.k[7];
+  d3.x ^= x12 + counter; d3.y ^= x13 + s.n0;    d3.z ^= x14 + s.n1;    d3.w ^= x15 + s.n2;
+  __stcs(dst + 0, d0); __stcs(dst + 1, d1); __stcs(dst + 2, d2); __stcs(dst + 3, d3);
+}
+
+// Arguments shared by the page kernels.
+struct PageArgs {
+  const ms_page *pages;   // entry list (list mode)
+  uint8_t *base;          // first page (range mode)
+  uint64_t first_id;      // id of the first page (range mode)
+  uint64_t n_pages;
+  const uint4 *key;       // 32-byte key in device memory
+  uint32_t domain;        // nonce word 15
+  unsigned int *status;   // device status word (kStatus* bits)
+  MulConsts mc;           // multipliers for kRotMul
+};
+
+__device__ __forceinline__ bool entry_ok(uint64_t addr) { return addr != 0 && (addr & 15u) == 0; }
+
+// K1, the one-launch bulk kernel.  Thread g works on page g / (64 / BPT) and,
+// inside it, on blocks t, t + 64/BPT, ... (t = g mod 64/BPT), so at each step
+// the threads of a warp touch consecutive 64-byte blocks of one page.
+template <int ROUNDS, int BPT, int UNR, int POL, bool RANGE>
+__global__ void __launch_bounds__(512) k_pages(const PageArgs a) {
+  constexpr uint32_t TPP = 64 / BPT;  // threads per page
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t page = g / TPP;
+  if (page >= a.n_pages) return;
+  const uint32_t t = (uint32_t)(g % TPP);
+
+  uint64_t addr, pid;
+  if (RANGE) {
+    addr = (uint64_t)a.base + page * (uint64_t)MS_PAGE_BYTES;
+    pid = a.first_id + page;
+  } else {
+    const ms_page e = a.pages[page];
+    addr = e.addr;
+    pid = e.page_id;
+    if (!entry_ok(addr)) {
+      if (t == 0) atomicOr(a.status, kStatusBadEntry);
+      return;
+    }
+  }
+  BlockSeed s;
+  load_key(a.key, s.k);
+  s.n0 = (uint32_t)pid;
+  s.n1 = (uint32_t)(pid >> 32);
+  s.n2 = a.domain;
+  uint4 *pg = reinterpret_cast<uint4 *>(addr);
+#pragma unroll 1
+  for (int b = 0; b < BPT; ++b) {
+    const uint32_t j = t + b * TPP;
+    xor_block<ROUNDS, UNR, POL>(pg + 4 * j, s, j, a.mc);
+  }
+}
+
+}  // namespace ms

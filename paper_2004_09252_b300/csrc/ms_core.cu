@@ -1,0 +1,407 @@
+// Context lifecycle, key placement, the one-launch entry points, ms_sync and
+// the streamed host-page form.
+#include <sys/random.h>
+#include <time.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <unordered_set>
+
+#include "ms_internal.h"
+
+namespace ms {
+
+int cuda_fail(ms_ctx *c, cudaError_t e) {
+  if (c) c->last_cuda.store((int)e);
+  return MS_ECUDA;
+}
+
+// Bounded wait on an event: poll, spinning for the first 50 us and then
+// sleeping 20 us between polls, until it completes or `timeout_ms` passes.
+int wait_event(ms_ctx *c, cudaEvent_t ev, uint32_t timeout_ms) {
+  using clk = std::chrono::steady_clock;
+  const auto t0 = clk::now();
+  const auto limit = std::chrono::milliseconds(timeout_ms);
+  for (;;) {
+    cudaError_t r = cudaEventQuery(ev);
+    if (r == cudaSuccess) return MS_OK;
+    if (r != cudaErrorNotReady) return cuda_fail(c, r);
+    const auto el = clk::now() - t0;
+    if (el > limit) return MS_ETIMEDOUT;
+    if (el > std::chrono::microseconds(50)) {
+      struct timespec ts = {0, 20000};
+      nanosleep(&ts, nullptr);
+    }
+  }
+}
+
+PageArgs make_args(const ms_ctx *c) {
+  PageArgs a{};
+  a.key = c->d_key;
+  a.domain = c->cfg.domain;
+  a.status = c->d_status;
+  a.mc.m12 = 1u << 12;
+  a.mc.m7 = 1u << 7;
+  return a;
+}
+
+}  // namespace ms
+
+using namespace ms;
+
+extern "C" {
+
+void ms_config_default(ms_config *cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->device = -1;
+  cfg->stream = nullptr;
+  cfg->domain = 0;
+  cfg->rounds = 20;
+  cfg->list_capacity = 65536;
+  cfg->timeout_ms = 10000;
+}
+
+const char *ms_strerror(int code) {
+  switch (code) {
+    case MS_OK: return "success";
+    case MS_EINVAL: return "invalid argument";
+    case MS_ENOTINIT: return "context not initialised";
+    case MS_ENOMEM: return "out of memory";
+    case MS_ECUDA: return "CUDA runtime error";
+    case MS_ETIMEDOUT: return "bounded wait timed out";
+    case MS_EBUSY: return "busy: admission refused";
+    case MS_ERANGE: return "size beyond the stated maximum";
+    default: return "unknown error";
+  }
+}
+
+int ms_last_cuda_error(const ms_ctx *ctx) { return ctx ? ctx->last_cuda.load() : 0; }
+
+static void release(ms_ctx *c) {
+  for (auto &s : c->slots) {
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.h) cudaFreeHost(s.h);
+    if (s.d) cudaFree(s.d);
+  }
+  for (int i = 0; i < kMaxHostStreams; ++i) {
+    if (c->hs_ev[i]) cudaEventDestroy(c->hs_ev[i]);
+    if (c->hs[i]) cudaStreamDestroy(c->hs[i]);
+    if (c->hs_buf[i]) cudaFree(c->hs_buf[i]);
+  }
+  if (c->sync_ev) cudaEventDestroy(c->sync_ev);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->d_status) cudaFree(c->d_status);
+  if (c->d_key) cudaFree(c->d_key);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg_in) {
+  if (!out) return MS_EINVAL;
+  *out = nullptr;
+  ms_config cfg;
+  if (cfg_in) cfg = *cfg_in; else ms_config_default(&cfg);
+  if (cfg.rounds == 0) cfg.rounds = 20;
+  if (cfg.rounds != 20 && cfg.rounds != 12 && cfg.rounds != 8) return MS_EINVAL;
+  if (cfg.list_capacity == 0) cfg.list_capacity = 65536;
+  if (cfg.timeout_ms == 0) cfg.timeout_ms = 10000;
+
+  int dev = cfg.device;
+  if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return MS_ECUDA;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || dev >= ndev) return MS_ECUDA;
+
+  ms_ctx *c = new (std::nothrow) ms_ctx();
+  if (!c) return MS_ENOMEM;
+  c->device = dev;
+  c->cfg = cfg;
+  c->cfg.device = dev;
+  DeviceGuard g(dev);
+  cudaError_t e;
+#define MS_TRY(call)                 \
+  do {                               \
+    e = (call);                      \
+    if (e != cudaSuccess) {          \
+      int rc = (e == cudaErrorMemoryAllocation) ? MS_ENOMEM : MS_ECUDA; \
+      release(c);                    \
+      return rc;                     \
+    }                                \
+  } while (0)
+
+  MS_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
+  if (cfg.stream) {
+    c->stream = (cudaStream_t)cfg.stream;
+  } else {
+    MS_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+  MS_TRY(cudaEventCreateWithFlags(&c->sync_ev, cudaEventDisableTiming));
+  MS_TRY(cudaMalloc(&c->d_status, sizeof(unsigned int)));
+  MS_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream));
+  MS_TRY(cudaHostAlloc(&c->h_status, sizeof(unsigned int), cudaHostAllocDefault));
+  for (auto &s : c->slots) {
+    MS_TRY(cudaHostAlloc(&s.h, sizeof(ms_page) * cfg.list_capacity, cudaHostAllocDefault));
+    MS_TRY(cudaMalloc(&s.d, sizeof(ms_page) * cfg.list_capacity));
+    MS_TRY(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+  }
+
+  // Key placement (Sec. 4.4: the key is drawn from the OS CSPRNG, handed to
+  // the GPU and purged from host memory).  The pinned bounce buffer is the
+  // only host copy the library makes; it is wiped before ms_init returns.
+  MS_TRY(cudaMalloc(&c->d_key, MS_KEY_BYTES));
+  uint8_t *bounce = nullptr;
+  MS_TRY(cudaHostAlloc(&bounce, MS_KEY_BYTES, cudaHostAllocDefault));
+  if (key) {
+    std::memcpy(bounce, key, MS_KEY_BYTES);
+  } else {
+    size_t got = 0;
+    while (got < MS_KEY_BYTES) {
+      ssize_t r = getrandom(bounce + got, MS_KEY_BYTES - got, 0);
+      if (r < 0) {
+        explicit_bzero(bounce, MS_KEY_BYTES);
+        cudaFreeHost(bounce);
+        release(c);
+        return MS_EINVAL;
+      }
+      got += (size_t)r;
+    }
+  }
+  e = cudaMemcpyAsync(c->d_key, bounce, MS_KEY_BYTES, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(c->sync_ev, c->stream);
+  int rc = (e == cudaSuccess) ? wait_event(c, c->sync_ev, cfg.timeout_ms) : MS_ECUDA;
+  explicit_bzero(bounce, MS_KEY_BYTES);
+  cudaFreeHost(bounce);
+  if (rc != MS_OK) {
+    release(c);
+    return rc;
+  }
+#undef MS_TRY
+
+  if (cfg.blocks_per_thread) c->tune.bpt = (int)cfg.blocks_per_thread;
+  if (cfg.threads_per_cta) c->tune.tpc = (int)cfg.threads_per_cta;
+  if (cfg.dr_unroll) c->tune.unr = (int)cfg.dr_unroll;
+  if (cfg.rounds != 20 && !cfg.dr_unroll) c->tune.unr = (int)cfg.rounds / 2;
+  if (!shape_available((int)cfg.rounds, c->tune)) {
+    release(c);
+    return MS_EINVAL;
+  }
+  c->alive = true;
+  *out = c;
+  return MS_OK;
+}
+
+static int submit_list_host(ms_ctx *c, const ms_page *pages, size_t n) {
+  if (!c || !c->alive) return MS_ENOTINIT;
+  if (n == 0) return MS_OK;
+  if (!pages) return MS_EINVAL;
+  for (size_t i = 0; i < n; ++i)
+    if (pages[i].addr == 0 || (pages[i].addr & 15u)) return MS_EINVAL;
+  if (c->cfg.check_duplicates) {
+    std::unordered_set<uint64_t> seen;
+    seen.reserve(n * 2);
+    for (size_t i = 0; i < n; ++i)
+      if (!seen.insert(pages[i].addr).second) return MS_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  const size_t cap = c->cfg.list_capacity;
+  for (size_t off = 0; off < n; off += cap) {
+    const size_t cnt = std::min(cap, n - off);
+    ListSlot &s = c->slots[c->next_slot];
+    c->next_slot = (c->next_slot + 1) % kListSlots;
+    if (s.used) {
+      int rc = wait_event(c, s.done, c->cfg.timeout_ms);
+      if (rc != MS_OK) return rc;
+    }
+    std::memcpy(s.h, pages + off, cnt * sizeof(ms_page));
+    cudaError_t e = cudaMemcpyAsync(s.d, s.h, cnt * sizeof(ms_page), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    PageArgs a = make_args(c);
+    a.pages = s.d;
+    a.n_pages = cnt;
+    e = launch_pages(c, a, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    e = cudaEventRecord(s.done, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    s.used = true;
+  }
+  return MS_OK;
+}
+
+int ms_encrypt_pages(ms_ctx *ctx, const ms_page *pages, size_t n) { return submit_list_host(ctx, pages, n); }
+int ms_decrypt_pages(ms_ctx *ctx, const ms_page *pages, size_t n) { return submit_list_host(ctx, pages, n); }
+
+static int submit_list_dev(ms_ctx *c, const ms_page *d_pages, size_t n) {
+  if (!c || !c->alive) return MS_ENOTINIT;
+  if (n == 0) return MS_OK;
+  if (!d_pages || ((uintptr_t)d_pages & 15u)) return MS_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  PageArgs a = make_args(c);
+  a.pages = d_pages;
+  a.n_pages = n;
+  cudaError_t e = launch_pages(c, a, c->stream);
+  return e == cudaSuccess ? MS_OK : cuda_fail(c, e);
+}
+
+int ms_encrypt_pages_dev(ms_ctx *ctx, const ms_page *d_pages, size_t n) { return submit_list_dev(ctx, d_pages, n); }
+int ms_decrypt_pages_dev(ms_ctx *ctx, const ms_page *d_pages, size_t n) { return submit_list_dev(ctx, d_pages, n); }
+
+int ms_crypt_range(ms_ctx *c, int op, void *d_base, uint64_t first_page_id, size_t n_pages) {
+  if (!c || !c->alive) return MS_ENOTINIT;
+  if (op != MS_ENCRYPT && op != MS_DECRYPT) return MS_EINVAL;
+  if (n_pages == 0) return MS_OK;
+  if (!d_base || ((uintptr_t)d_base & 15u)) return MS_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  PageArgs a = make_args(c);
+  a.base = (uint8_t *)d_base;
+  a.first_id = first_page_id;
+  a.n_pages = n_pages;
+  cudaError_t e = launch_pages(c, a, c->stream);
+  return e == cudaSuccess ? MS_OK : cuda_fail(c, e);
+}
+
+int ms_sync(ms_ctx *c) {
+  if (!c || !c->alive) return MS_ENOTINIT;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(c->sync_ev, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  int rc = wait_event(c, c->sync_ev, c->cfg.timeout_ms);
+  if (rc != MS_OK) return rc;
+  const unsigned st = *(volatile unsigned int *)c->h_status;
+  *c->h_status = 0;
+  return (st & kStatusBadEntry) ? MS_EINVAL : MS_OK;
+}
+
+int ms_shutdown(ms_ctx *c) {
+  if (!c) return MS_OK;
+  int rc = MS_OK;
+  {
+    DeviceGuard g(c->device);
+    if (c->alive) {
+      // finish queued work (bounded), then overwrite the key on the device
+      cudaEventRecord(c->sync_ev, c->stream);
+      rc = wait_event(c, c->sync_ev, c->cfg.timeout_ms);
+      if (c->d_key) cudaMemsetAsync(c->d_key, 0, MS_KEY_BYTES, c->stream);
+      cudaEventRecord(c->sync_ev, c->stream);
+      int rc2 = wait_event(c, c->sync_ev, c->cfg.timeout_ms);
+      if (rc == MS_OK) rc = rc2;
+      for (int i = 0; i < kMaxHostStreams; ++i)
+        if (c->hs[i]) cudaStreamSynchronize(c->hs[i]);
+    }
+    c->alive = false;
+    release(c);
+  }
+  return rc;
+}
+
+int ms_get_shape(const ms_ctx *c, ms_shape *out) {
+  if (!c || !c->alive) return MS_ENOTINIT;
+  if (!out) return MS_EINVAL;
+  out->blocks_per_thread = (uint32_t)c->tune.bpt;
+  out->threads_per_cta = (uint32_t)c->tune.tpc;
+  out->dr_unroll = (uint32_t)c->tune.unr;
+  out->rot_policy = (uint32_t)c->tune.pol;
+  return MS_OK;
+}
+
+int ms_set_shape(ms_ctx *c, const ms_shape *sh) {
+  if (!c || !c->alive) return MS_ENOTINIT;
+  if (!sh) return MS_EINVAL;
+  Tune t;
+  t.bpt = (int)sh->blocks_per_thread;
+  t.tpc = (int)sh->threads_per_cta;
+  t.unr = (int)sh->dr_unroll;
+  t.pol = (int)sh->rot_policy;
+  if (!shape_available((int)c->cfg.rounds, t)) return MS_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->tune = t;
+  return MS_OK;
+}
+
+// ---------------------------------------------------------------- host pages
+int ms_crypt_host(ms_ctx *c, int op, void *host_base, uint64_t first_page_id, size_t n_pages,
+                  size_t chunk_bytes, int n_streams) {
+  if (!c || !c->alive) return MS_ENOTINIT;
+  if (op != MS_ENCRYPT && op != MS_DECRYPT) return MS_EINVAL;
+  if (n_pages == 0) return MS_OK;
+  if (!host_base) return MS_EINVAL;
+  if (chunk_bytes == 0) chunk_bytes = (size_t)16 << 20;
+  if (chunk_bytes % MS_PAGE_BYTES) return MS_EINVAL;
+  if (n_streams == 0) n_streams = 2;
+  if (n_streams < 1 || n_streams > kMaxHostStreams) return MS_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaError_t e;
+  if (c->hs_cap < chunk_bytes) {
+    for (int i = 0; i < kMaxHostStreams; ++i) {
+      if (c->hs_buf[i]) {
+        if (c->hs[i]) cudaStreamSynchronize(c->hs[i]);
+        cudaFree(c->hs_buf[i]);
+        c->hs_buf[i] = nullptr;
+      }
+    }
+    c->hs_cap = 0;
+  }
+  for (int i = 0; i < n_streams; ++i) {
+    if (!c->hs[i]) {
+      e = cudaStreamCreateWithFlags(&c->hs[i], cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(c, e);
+      e = cudaEventCreateWithFlags(&c->hs_ev[i], cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    if (!c->hs_buf[i]) {
+      e = cudaMalloc(&c->hs_buf[i], chunk_bytes);
+      if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MS_ENOMEM : cuda_fail(c, e);
+    }
+  }
+  c->hs_cap = std::max(c->hs_cap, chunk_bytes);
+  // order after earlier work on the context stream
+  e = cudaEventRecord(c->sync_ev, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  for (int i = 0; i < n_streams; ++i) cudaStreamWaitEvent(c->hs[i], c->sync_ev, 0);
+
+  const size_t pages_per_chunk = chunk_bytes / MS_PAGE_BYTES;
+  uint8_t *hb = (uint8_t *)host_base;
+  size_t chunk = 0;
+  for (size_t p0 = 0; p0 < n_pages; p0 += pages_per_chunk, ++chunk) {
+    const int si = (int)(chunk % n_streams);
+    const size_t np = std::min(pages_per_chunk, n_pages - p0);
+    const size_t bytes = np * MS_PAGE_BYTES;
+    cudaStream_t s = c->hs[si];
+    e = cudaMemcpyAsync(c->hs_buf[si], hb + p0 * MS_PAGE_BYTES, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    PageArgs a = make_args(c);
+    a.base = (uint8_t *)c->hs_buf[si];
+    a.first_id = first_page_id + p0;
+    a.n_pages = np;
+    e = launch_pages(c, a, s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    e = cudaMemcpyAsync(hb + p0 * MS_PAGE_BYTES, c->hs_buf[si], bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+  }
+  const uint64_t n_chunks = chunk;
+  int rc = MS_OK;
+  for (int i = 0; i < n_streams && (uint64_t)i < n_chunks; ++i) {
+    e = cudaEventRecord(c->hs_ev[i], c->hs[i]);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+  }
+  // bound: timeout_ms per chunk
+  const uint64_t limit = (uint64_t)c->cfg.timeout_ms * std::max<uint64_t>(1, n_chunks);
+  for (int i = 0; i < n_streams && (uint64_t)i < n_chunks; ++i) {
+    int r = wait_event(c, c->hs_ev[i], (uint32_t)std::min<uint64_t>(limit, 0xffffffffu));
+    if (r != MS_OK && rc == MS_OK) rc = r;
+  }
+  return rc;
+}
+
+}  // extern "C"

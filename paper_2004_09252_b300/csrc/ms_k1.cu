@@ -1,0 +1,77 @@
+// K1 variant table: every compiled (rounds, blocks/thread, unroll, rotation
+// policy, list|range) instance of the bulk page kernel, and its launcher.
+#include "ms_internal.h"
+
+namespace ms {
+namespace {
+
+using LaunchFn = cudaError_t (*)(const PageArgs &, int, cudaStream_t);
+
+template <int R, int B, int U, int P, bool RG>
+cudaError_t launch_k1(const PageArgs &a, int tpc, cudaStream_t s) {
+  constexpr uint64_t TPP = 64 / B;
+  const uint64_t threads = a.n_pages * TPP;
+  const uint64_t grid = (threads + tpc - 1) / tpc;
+  if (grid > 0x7fffffffull) return cudaErrorInvalidConfiguration;
+  k_pages<R, B, U, P, RG><<<(unsigned)grid, tpc, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+struct Entry {
+  int rounds, bpt, unr, pol;
+  LaunchFn list_fn, range_fn;
+};
+
+#define MS_K1(R, B, U, P) {R, B, U, P, &launch_k1<R, B, U, P, false>, &launch_k1<R, B, U, P, true>}
+
+const Entry kTable[] = {
+    // ChaCha20, the paper's cipher: the tuned search space.
+    MS_K1(20, 1, 1, 0), MS_K1(20, 1, 2, 0), MS_K1(20, 1, 10, 0),
+    MS_K1(20, 1, 1, 1), MS_K1(20, 1, 2, 1), MS_K1(20, 1, 10, 1),
+    MS_K1(20, 1, 1, 2), MS_K1(20, 1, 2, 2), MS_K1(20, 1, 10, 2),
+    MS_K1(20, 2, 2, 0), MS_K1(20, 2, 10, 0),
+    MS_K1(20, 2, 2, 1), MS_K1(20, 2, 10, 1),
+    MS_K1(20, 2, 2, 2), MS_K1(20, 2, 10, 2),
+    MS_K1(20, 4, 2, 1), MS_K1(20, 4, 10, 1),
+    MS_K1(20, 4, 2, 2), MS_K1(20, 4, 10, 2),
+    // Reduced-round variants.
+    MS_K1(12, 1, 6, 1), MS_K1(12, 2, 6, 1), MS_K1(12, 1, 2, 1),
+    MS_K1(8, 1, 4, 1), MS_K1(8, 2, 4, 1), MS_K1(8, 1, 2, 1),
+};
+
+#undef MS_K1
+
+const Entry *find(int rounds, const Tune &t) {
+  for (const Entry &e : kTable)
+    if (e.rounds == rounds && e.bpt == t.bpt && e.unr == t.unr && e.pol == t.pol) return &e;
+  return nullptr;
+}
+
+}  // namespace
+
+bool shape_available(int rounds, const Tune &t) {
+  return find(rounds, t) != nullptr && (t.tpc == 128 || t.tpc == 256 || t.tpc == 512);
+}
+
+cudaError_t launch_pages_shape(const PageArgs &a, int rounds, const Tune &t, bool range,
+                               cudaStream_t s) {
+  const Entry *e = find(rounds, t);
+  if (!e) return cudaErrorInvalidValue;
+  if (a.n_pages == 0) return cudaSuccess;
+  return (range ? e->range_fn : e->list_fn)(a, t.tpc, s);
+}
+
+cudaError_t launch_pages(const ms_ctx *c, const PageArgs &a, cudaStream_t s) {
+  return launch_pages_shape(a, (int)c->cfg.rounds, c->tune, a.pages == nullptr, s);
+}
+
+// Every compiled shape, for the autotuner.
+int k1_shape_count() { return (int)(sizeof(kTable) / sizeof(kTable[0])); }
+void k1_shape(int i, int *rounds, Tune *t) {
+  *rounds = kTable[i].rounds;
+  t->bpt = kTable[i].bpt;
+  t->unr = kTable[i].unr;
+  t->pol = kTable[i].pol;
+}
+
+}  // namespace ms

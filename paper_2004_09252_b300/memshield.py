@@ -1,0 +1,221 @@
+"""Thin ctypes binding of libmemshield.so (the C ABI in include/memshield.h).
+
+Argument marshalling only: every step of the page cipher runs in the CUDA
+library.  Functions keep the C names; pointers are passed as Python ints
+(``tensor.data_ptr()``, ``ndarray.ctypes.data``) and errors become
+``MemShieldError``.  Importing this module loads the library and fails loudly
+if it is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MS_PAGE_BYTES = 4096
+MS_BLOCKS_PER_PAGE = 64
+MS_KEY_BYTES = 32
+MS_OK, MS_EINVAL, MS_ENOTINIT, MS_ENOMEM, MS_ECUDA, MS_ETIMEDOUT, MS_EBUSY, MS_ERANGE = 0, -1, -2, -3, -4, -5, -6, -7
+MS_ENCRYPT, MS_DECRYPT = 0, 1
+
+PAGE_DTYPE = np.dtype([("addr", "<u8"), ("page_id", "<u8")])
+
+
+class MemShieldError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+class ms_config(ctypes.Structure):
+    _fields_ = [
+        ("device", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+        ("domain", ctypes.c_uint32),
+        ("rounds", ctypes.c_uint32),
+        ("list_capacity", ctypes.c_uint32),
+        ("timeout_ms", ctypes.c_uint32),
+        ("blocks_per_thread", ctypes.c_uint32),
+        ("threads_per_cta", ctypes.c_uint32),
+        ("dr_unroll", ctypes.c_uint32),
+        ("check_duplicates", ctypes.c_uint32),
+    ]
+
+
+class ms_shape(ctypes.Structure):
+    _fields_ = [
+        ("blocks_per_thread", ctypes.c_uint32),
+        ("threads_per_cta", ctypes.c_uint32),
+        ("dr_unroll", ctypes.c_uint32),
+        ("rot_policy", ctypes.c_uint32),
+    ]
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        if os.environ.get("MEMSHIELD_NO_BUILD"):
+            raise ImportError(f"libmemshield.so not built at {path}")
+        _build.build()
+    elif _build.needs_build() and not os.environ.get("MEMSHIELD_NO_BUILD"):
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, S, I, U64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint64
+    sig = {
+        "ms_config_default": (None, [ctypes.POINTER(ms_config)]),
+        "ms_init": (I, [ctypes.POINTER(P), P, ctypes.POINTER(ms_config)]),
+        "ms_encrypt_pages": (I, [P, P, S]),
+        "ms_decrypt_pages": (I, [P, P, S]),
+        "ms_encrypt_pages_dev": (I, [P, P, S]),
+        "ms_decrypt_pages_dev": (I, [P, P, S]),
+        "ms_crypt_range": (I, [P, I, P, U64, S]),
+        "ms_sync": (I, [P]),
+        "ms_shutdown": (I, [P]),
+        "ms_strerror": (ctypes.c_char_p, [I]),
+        "ms_last_cuda_error": (I, [P]),
+        "ms_crypt_host": (I, [P, I, P, U64, S, S, I]),
+        "ms_get_shape": (I, [P, ctypes.POINTER(ms_shape)]),
+        "ms_set_shape": (I, [P, ctypes.POINTER(ms_shape)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+lib = _lib
+
+
+def strerror(code: int) -> str:
+    return _lib.ms_strerror(code).decode()
+
+
+def _check(code: int, where: str) -> int:
+    if code != MS_OK:
+        raise MemShieldError(code, where)
+    return code
+
+
+def config_default() -> ms_config:
+    cfg = ms_config()
+    _lib.ms_config_default(ctypes.byref(cfg))
+    return cfg
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def pages_array(addrs, page_ids) -> np.ndarray:
+    """Pack (addr, page_id) pairs into the 16-byte ms_page layout."""
+    a = np.empty(len(addrs), dtype=PAGE_DTYPE)
+    a["addr"] = np.asarray(addrs, dtype=np.uint64)
+    a["page_id"] = np.asarray(page_ids, dtype=np.uint64)
+    return a
+
+
+class Context:
+    """An ms_ctx: the key on one device plus the stream the work runs on."""
+
+    def __init__(self, key: bytes | None = None, *, device: int = -1, stream=None, domain: int = 0,
+                 rounds: int = 20, list_capacity: int = 0, timeout_ms: int = 0,
+                 blocks_per_thread: int = 0, threads_per_cta: int = 0, dr_unroll: int = 0,
+                 check_duplicates: bool = False):
+        cfg = config_default()
+        cfg.device = device
+        if stream is not None:
+            cfg.stream = stream if isinstance(stream, int) else stream.cuda_stream
+        cfg.domain = domain
+        cfg.rounds = rounds
+        if list_capacity:
+            cfg.list_capacity = list_capacity
+        if timeout_ms:
+            cfg.timeout_ms = timeout_ms
+        cfg.blocks_per_thread = blocks_per_thread
+        cfg.threads_per_cta = threads_per_cta
+        cfg.dr_unroll = dr_unroll
+        cfg.check_duplicates = 1 if check_duplicates else 0
+        h = ctypes.c_void_p()
+        kb = None
+        if key is not None:
+            if len(key) != MS_KEY_BYTES:
+                raise ValueError("key must be 32 bytes")
+            kb = ctypes.create_string_buffer(bytes(key), MS_KEY_BYTES)
+        _check(_lib.ms_init(ctypes.byref(h), kb, ctypes.byref(cfg)), "ms_init")
+        if kb is not None:
+            ctypes.memset(kb, 0, MS_KEY_BYTES)
+        self.handle = h.value
+        self.cfg = cfg
+
+    # -- one-launch forms
+    def encrypt_pages(self, pages: np.ndarray) -> None:
+        pages = np.ascontiguousarray(pages, dtype=PAGE_DTYPE)
+        _check(_lib.ms_encrypt_pages(self.handle, pages.ctypes.data, pages.size), "ms_encrypt_pages")
+
+    def decrypt_pages(self, pages: np.ndarray) -> None:
+        pages = np.ascontiguousarray(pages, dtype=PAGE_DTYPE)
+        _check(_lib.ms_decrypt_pages(self.handle, pages.ctypes.data, pages.size), "ms_decrypt_pages")
+
+    def encrypt_pages_dev(self, d_pages, n: int) -> None:
+        _check(_lib.ms_encrypt_pages_dev(self.handle, _ptr(d_pages), n), "ms_encrypt_pages_dev")
+
+    def decrypt_pages_dev(self, d_pages, n: int) -> None:
+        _check(_lib.ms_decrypt_pages_dev(self.handle, _ptr(d_pages), n), "ms_decrypt_pages_dev")
+
+    def crypt_range(self, op: int, d_base, first_page_id: int, n_pages: int) -> None:
+        _check(_lib.ms_crypt_range(self.handle, op, _ptr(d_base), first_page_id, n_pages), "ms_crypt_range")
+
+    def crypt_host(self, op: int, host_base, first_page_id: int, n_pages: int, chunk_bytes: int = 0,
+                   n_streams: int = 0) -> None:
+        _check(_lib.ms_crypt_host(self.handle, op, _ptr(host_base), first_page_id, n_pages, chunk_bytes,
+                                  n_streams), "ms_crypt_host")
+
+    def get_shape(self) -> dict:
+        sh = ms_shape()
+        _check(_lib.ms_get_shape(self.handle, ctypes.byref(sh)), "ms_get_shape")
+        return {f: getattr(sh, f) for f, _ in ms_shape._fields_}
+
+    def set_shape(self, blocks_per_thread: int, threads_per_cta: int, dr_unroll: int, rot_policy: int) -> None:
+        sh = ms_shape(blocks_per_thread, threads_per_cta, dr_unroll, rot_policy)
+        _check(_lib.ms_set_shape(self.handle, ctypes.byref(sh)), "ms_set_shape")
+
+    def sync(self) -> int:
+        return _lib.ms_sync(self.handle)
+
+    def sync_checked(self) -> None:
+        _check(self.sync(), "ms_sync")
+
+    def last_cuda_error(self) -> int:
+        return _lib.ms_last_cuda_error(self.handle)
+
+    def shutdown(self) -> int:
+        if self.handle:
+            rc = _lib.ms_shutdown(self.handle)
+            self.handle = None
+            return rc
+        return MS_OK
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.shutdown()
+
+    def __del__(self):
+        try:
+            self.shutdown()
+        except Exception:
+            pass

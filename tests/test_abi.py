@@ -1,0 +1,79 @@
+"""The C ABI without a GPU: the library loads, exports every declared entry
+point, and its structs have the layout the binding assumes."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+INCLUDE = os.path.join(ROOT, "include")
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(INCLUDE):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(INCLUDE, fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(ms_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_paper_calls():
+    names = declared_functions()
+    for must in ("ms_init", "ms_encrypt_pages", "ms_decrypt_pages", "ms_sync", "ms_shutdown", "ms_strerror"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2004_09252_b300 import memshield
+    missing = [n for n in declared_functions() if not hasattr(memshield.lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", memshield._build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b[TW] (ms_[a-z0-9_]+)$", out, flags=re.M))
+    assert set(declared_functions()) <= exported
+
+
+def test_strerror_and_defaults():
+    from paper_2004_09252_b300 import memshield as m
+    assert m.strerror(m.MS_OK) == "success"
+    assert "timed out" in m.strerror(m.MS_ETIMEDOUT)
+    assert m.strerror(-999) == "unknown error"
+    cfg = m.config_default()
+    assert cfg.rounds == 20 and cfg.device == -1 and cfg.domain == 0 and cfg.timeout_ms > 0
+
+
+def test_null_context_is_rejected_without_gpu():
+    from paper_2004_09252_b300 import memshield as m
+    assert m.lib.ms_sync(None) == m.MS_ENOTINIT
+    assert m.lib.ms_encrypt_pages(None, None, 0) == m.MS_ENOTINIT
+    assert m.lib.ms_shutdown(None) == m.MS_OK
+    assert m.lib.ms_init(None, None, None) == m.MS_EINVAL
+
+
+def test_struct_layout_matches_c():
+    from paper_2004_09252_b300 import memshield as m
+    src = r'''
+    #include <stdio.h>
+    #include <stddef.h>
+    #include "memshield.h"
+    int main(void) {
+      printf("%zu %zu %zu %zu %zu %zu\n", sizeof(ms_page), sizeof(ms_config),
+             offsetof(ms_config, stream), offsetof(ms_config, domain),
+             offsetof(ms_config, timeout_ms), offsetof(ms_config, check_duplicates));
+      return 0;
+    }'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", INCLUDE, c, "-o", exe])
+        vals = [int(v) for v in subprocess.check_output([exe]).split()]
+    cfg = m.ms_config
+    assert vals == [m.PAGE_DTYPE.itemsize, ctypes.sizeof(cfg), cfg.stream.offset, cfg.domain.offset,
+                    cfg.timeout_ms.offset, cfg.check_duplicates.offset]

@@ -1,0 +1,203 @@
+"""GPU parity of the one-launch page kernel (K1) against the CPU oracle: bit-exact."""
+import numpy as np
+import pytest
+
+import synth
+from helpers import PAGE, oracle_expected, oracle_pages, sample_pages
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ms():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2004_09252_b300 import memshield
+    return memshield
+
+
+def dev(a: np.ndarray):
+    return torch.from_numpy(a).cuda()
+
+
+def make_ctx(ms, key, **kw):
+    return ms.Context(key, stream=torch.cuda.current_stream().cuda_stream, **kw)
+
+
+def test_small_config_encrypt_then_decrypt(ms, key1):
+    """256 pages of seed 0, ids 0..255, one encrypt launch then one decrypt launch."""
+    n = 256
+    plain = synth.page_bytes(0, 0, n)
+    d = dev(plain)
+    base = d.data_ptr()
+    ids = np.arange(n, dtype=np.uint64)
+    pages = ms.pages_array(base + PAGE * ids, ids)
+    with make_ctx(ms, key1) as ctx:
+        ctx.encrypt_pages(pages)
+        ctx.sync_checked()
+        got = d.cpu().numpy()
+        want = oracle_expected(key1, plain, ids, ids)
+        assert np.array_equal(got, want)
+        ctx.decrypt_pages(pages)
+        ctx.sync_checked()
+        assert np.array_equal(d.cpu().numpy(), plain)
+
+
+SHAPES = [(b, u, p) for (b, u, p) in [
+    (1, 1, 0), (1, 2, 0), (1, 10, 0), (1, 1, 1), (1, 2, 1), (1, 10, 1), (1, 1, 2), (1, 2, 2), (1, 10, 2),
+    (2, 2, 0), (2, 10, 0), (2, 2, 1), (2, 10, 1), (2, 2, 2), (2, 10, 2),
+    (4, 2, 1), (4, 10, 1), (4, 2, 2), (4, 10, 2)]]
+
+
+@pytest.mark.parametrize("bpt,unr,pol", SHAPES)
+@pytest.mark.parametrize("tpc", [128, 512])
+def test_every_shape_scattered_ragged(ms, key1, bpt, unr, pol, tpc):
+    """Every compiled shape on a ragged, scattered list with ids that differ from slots."""
+    n_slots, n = 97, 61                      # 61 pages: several CTAs and a ragged tail
+    plain = synth.page_bytes(7, 0, n_slots)
+    d = dev(plain)
+    slots = synth.scattered_slots(8, n_slots, n)
+    ids = (synth.splitmix64(9, 0, n)).astype(np.uint64)   # full 64-bit ids
+    pages = ms.pages_array(d.data_ptr() + PAGE * slots.astype(np.uint64), ids)
+    with make_ctx(ms, key1) as ctx:
+        ctx.set_shape(bpt, tpc, unr, pol)
+        assert ctx.get_shape() == {"blocks_per_thread": bpt, "threads_per_cta": tpc, "dr_unroll": unr,
+                                   "rot_policy": pol}
+        ctx.encrypt_pages(pages)
+        ctx.sync_checked()
+    assert np.array_equal(d.cpu().numpy(), oracle_expected(key1, plain, slots, ids))
+
+
+@pytest.mark.parametrize("rounds", [8, 12])
+def test_reduced_rounds(ms, key1, rounds):
+    n = 33
+    plain = synth.page_bytes(10, 0, n)
+    d = dev(plain)
+    ids = np.arange(100, 100 + n, dtype=np.uint64)
+    slots = np.arange(n, dtype=np.uint64)
+    with make_ctx(ms, key1, rounds=rounds) as ctx:
+        ctx.encrypt_pages(ms.pages_array(d.data_ptr() + PAGE * slots, ids))
+        ctx.sync_checked()
+    assert np.array_equal(d.cpu().numpy(), oracle_expected(key1, plain, slots, ids, rounds=rounds))
+
+
+def test_domain_word(ms, key1):
+    n = 8
+    plain = synth.page_bytes(11, 0, n)
+    d = dev(plain)
+    ids = np.arange(n, dtype=np.uint64)
+    with make_ctx(ms, key1, domain=0xDEADBEEF) as ctx:
+        ctx.encrypt_pages(ms.pages_array(d.data_ptr() + PAGE * ids, ids))
+        ctx.sync_checked()
+    assert np.array_equal(d.cpu().numpy(), oracle_expected(key1, plain, ids, ids, domain=0xDEADBEEF))
+
+
+def test_device_list_and_range_forms(ms, key1):
+    n = 130
+    plain = synth.page_bytes(12, 0, n)
+    ids = np.arange(5000, 5000 + n, dtype=np.uint64)
+    slots = np.arange(n, dtype=np.uint64)
+    want = oracle_expected(key1, plain, slots, ids)
+    with make_ctx(ms, key1) as ctx:
+        d = dev(plain)
+        lst = torch.from_numpy(ms.pages_array(d.data_ptr() + PAGE * slots, ids).view(np.uint8)).cuda()
+        ctx.encrypt_pages_dev(lst, n)
+        assert ctx.sync() == 0
+        assert np.array_equal(d.cpu().numpy(), want)
+        d2 = dev(plain)
+        ctx.crypt_range(ms.MS_ENCRYPT, d2, 5000, n)
+        assert ctx.sync() == 0
+        assert np.array_equal(d2.cpu().numpy(), want)
+        ctx.crypt_range(ms.MS_DECRYPT, d2, 5000, n)
+        assert ctx.sync() == 0
+        assert np.array_equal(d2.cpu().numpy(), plain)
+
+
+def test_empty_and_bad_entries(ms, key1):
+    n = 4
+    plain = synth.page_bytes(13, 0, n)
+    d = dev(plain)
+    ids = np.arange(n, dtype=np.uint64)
+    with make_ctx(ms, key1) as ctx:
+        ctx.encrypt_pages(ms.pages_array([], []))          # n = 0 is a no-op
+        ctx.crypt_range(ms.MS_ENCRYPT, d, 0, 0)
+        assert ctx.sync() == 0
+        assert np.array_equal(d.cpu().numpy(), plain)
+        bad = ms.pages_array(d.data_ptr() + PAGE * ids, ids)
+        bad["addr"][2] += 8                                  # misaligned: rejected on the host
+        with pytest.raises(ms.MemShieldError) as e:
+            ctx.encrypt_pages(bad)
+        assert e.value.code == ms.MS_EINVAL
+        assert ctx.sync() == 0
+        assert np.array_equal(d.cpu().numpy(), plain)       # nothing was launched
+        # device-side check: the bad entry is skipped, the others are processed
+        lst = ms.pages_array(d.data_ptr() + PAGE * ids, ids)
+        lst["addr"][1] = 0
+        dl = torch.from_numpy(lst.view(np.uint8)).cuda()
+        ctx.encrypt_pages_dev(dl, n)
+        assert ctx.sync() == ms.MS_EINVAL
+        assert ctx.sync() == 0                               # the status word was cleared
+        want = oracle_expected(key1, plain, np.array([0, 2, 3], np.uint64), np.array([0, 2, 3], np.uint64))
+        assert np.array_equal(d.cpu().numpy(), want)
+        with pytest.raises(ms.MemShieldError):
+            ctx.crypt_range(7, d, 0, 1)                      # bad op
+
+
+def test_duplicate_check(ms, key1):
+    plain = synth.page_bytes(14, 0, 2)
+    d = dev(plain)
+    with make_ctx(ms, key1, check_duplicates=True) as ctx:
+        dup = ms.pages_array([d.data_ptr(), d.data_ptr()], [0, 1])
+        with pytest.raises(ms.MemShieldError):
+            ctx.encrypt_pages(dup)
+
+
+def test_list_longer_than_staging_slot(ms, key1):
+    """A host list longer than one staging slot is cut into several launches."""
+    n = 300
+    plain = synth.page_bytes(15, 0, n)
+    d = dev(plain)
+    ids = np.arange(n, dtype=np.uint64)
+    with make_ctx(ms, key1, list_capacity=64) as ctx:
+        for _ in range(3):                                   # odd count: encrypted once net
+            ctx.encrypt_pages(ms.pages_array(d.data_ptr() + PAGE * ids, ids))
+        ctx.sync_checked()
+    assert np.array_equal(d.cpu().numpy(), oracle_expected(key1, plain, ids, ids))
+
+
+@pytest.mark.slow
+def test_bulk_1gib_sampled(ms, key1):
+    """The 1 GiB bulk configuration in the launch shape the benchmark times:
+    262,144 pages of seed 2, ids 0..262143, one encrypt then one decrypt launch.
+    Sampled pages are checked against the oracle; the round trip is checked whole."""
+    n = 262144
+    plain = synth.page_bytes_fast(2, 0, n)
+    d = dev(plain)
+    ids = np.arange(n, dtype=np.uint64)
+    lst = torch.from_numpy(ms.pages_array(d.data_ptr() + PAGE * ids, ids).view(np.uint8)).cuda()
+    with make_ctx(ms, key1) as ctx:
+        ctx.encrypt_pages_dev(lst, n)
+        ctx.sync_checked()
+        sample = sample_pages(21, n, 48)
+        got = d.view(n, PAGE)[torch.from_numpy(sample).cuda()].cpu().numpy()
+        assert np.array_equal(got, oracle_pages(key1, 2, sample, sample))
+        ctx.decrypt_pages_dev(lst, n)
+        ctx.sync_checked()
+        assert torch.equal(d, torch.from_numpy(plain).cuda())
+
+
+def test_host_streamed_pages(ms, key1):
+    """Host pages streamed through the device in chunks on two streams."""
+    n = 3000                                                   # 11.7 MiB, ragged last chunk
+    plain = synth.page_bytes_fast(4, 0, n)
+    h = torch.from_numpy(plain.copy()).pin_memory()
+    with make_ctx(ms, key1) as ctx:
+        ctx.crypt_host(ms.MS_ENCRYPT, h, 0, n, chunk_bytes=2 << 20, n_streams=2)
+        sample = sample_pages(22, n, 64)
+        assert np.array_equal(h.numpy().reshape(n, PAGE)[sample], oracle_pages(key1, 4, sample, sample))
+        for ns in (1, 3, 4):
+            ctx.crypt_host(ms.MS_DECRYPT, h, 0, n, chunk_bytes=4096 * 7, n_streams=ns)
+            ctx.crypt_host(ms.MS_ENCRYPT, h, 0, n, chunk_bytes=1 << 20, n_streams=ns)
+        ctx.crypt_host(ms.MS_DECRYPT, h, 0, n)
+        assert np.array_equal(h.numpy(), plain)
