@@ -105,8 +105,10 @@ class ClockSampler:
                 h = pynvml.nvmlDeviceGetHandleByIndex(torch_dev)
             self.nvml, self.h = pynvml, h
             self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
-        except Exception as e:  # no NVML: report the absence
-            self.nvml, self.h, self.err = None, None, str(e)
+        except Exception as e:  # no NVML binding: fall back to nvidia-smi sampling
+            self.nvml, self.h, self.err = None, None, f"{type(e).__name__}: {e}"
+        self.smi = None
+        self.smi_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(torch_dev)).split(",")[0] or "0"
 
     def _run(self):
         n = self.nvml
@@ -128,18 +130,46 @@ class ClockSampler:
         if self.nvml:
             self._t = threading.Thread(target=self._run, daemon=True)
             self._t.start()
+        else:
+            import subprocess
+            try:
+                self.smi = subprocess.Popen(
+                    ["nvidia-smi", "-i", self.smi_index, "--query-gpu=clocks.sm,clocks.max.sm,"
+                     "clocks_event_reasons.active", "--format=csv,noheader,nounits", "-lms", "50"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except Exception as e:
+                self.err += f"; nvidia-smi: {e}"
         return self
 
     def __exit__(self, *a):
         self._stop.set()
         if self._t:
             self._t.join()
+        if self.smi:
+            self.smi.terminate()
+            out, _ = self.smi.communicate(timeout=10)
+            for line in out.splitlines():
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 3:
+                    continue
+                try:
+                    self.samples.append(float(parts[0]))
+                    self.max_mhz = float(parts[1])
+                    r = int(parts[2], 16)
+                except ValueError:
+                    continue
+                for bit, name in REASONS.items():
+                    if r & bit and name != "gpu_idle":
+                        self.reasons.add(name)
 
     def summary(self):
+        src = "nvml" if self.nvml else ("nvidia-smi" if self.smi else "none")
+        out = {"sm_mhz": statistics.median(self.samples) if self.samples else None,
+               "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons), "samples": len(self.samples),
+               "source": src}
         if not self.nvml:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": "NVML unavailable"}
-        return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
-                "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons), "samples": len(self.samples)}
+            out["nvml_error"] = self.err
+        return out
 
 
 # --------------------------------------------------------------- CPU oracle
@@ -159,10 +189,15 @@ def cpu_oracle_rate(seconds: float, threads: int):
     n = int(max(threads * 8, min(BULK_PAGES, seconds / per_page * threads)))
     buf = synth.page_bytes_fast(2, 0, n)
     ids = np.arange(n, dtype=np.uint64)
+    passes = 0
     t0 = time.perf_counter()
-    oracle.crypt_pages(key, buf, ids, ids, threads=threads)
-    dt = time.perf_counter() - t0
-    return n * PAGE / dt / 1e9, n, dt
+    while True:                      # whole passes until `seconds` of wall time
+        oracle.crypt_pages(key, buf, ids, ids, threads=threads)
+        passes += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds or passes >= 64:
+            break
+    return passes * n * PAGE / dt / 1e9, n, dt, passes
 
 
 def host_cores():
@@ -307,10 +342,11 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         threads = host_cores()
-        v, npg, dt = cpu_oracle_rate(args.cpu_seconds, threads)
+        v, npg, dt, passes = cpu_oracle_rate(args.cpu_seconds, threads)
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
                                 "sample": f"{npg} pages ({npg * PAGE / 2**20:.0f} MiB) of the bulk buffer, "
-                                          f"one encrypt pass, {dt:.1f} s, pages split over {threads} threads"}
+                                          f"{passes} encrypt passes in {dt:.1f} s, pages split over "
+                                          f"{threads} threads"}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

@@ -73,7 +73,7 @@ typedef struct ms_ctx ms_ctx;
 
 typedef struct ms_config {
   int device;                  /* CUDA device ordinal; -1 = the calling thread's current device */
-  void *stream;                /* cudaStream_t to launch on; NULL = a stream the library creates */
+  void *stream;                /* cudaStream_t to launch on (see use_stream) */
   uint32_t domain;             /* nonce word 15 (the paper's client PID); default 0 */
   uint32_t rounds;             /* 20 (default), or 8 / 12 */
   uint32_t list_capacity;      /* entries per host-list staging slot (default 65536) */
@@ -82,6 +82,8 @@ typedef struct ms_config {
   uint32_t threads_per_cta;    /* 0 = tuned default; else 128, 256 or 512 */
   uint32_t dr_unroll;          /* 0 = tuned default; else double rounds per loop trip: 1, 2 or rounds/2 */
   uint32_t check_duplicates;   /* nonzero: host-list calls reject a page address listed twice */
+  uint32_t use_stream;         /* nonzero: launch on `stream` even when it is NULL (the legacy
+                                  default stream); zero and stream == NULL: the library's own stream */
 } ms_config;
 
 /* Fill *cfg with the defaults listed above. */

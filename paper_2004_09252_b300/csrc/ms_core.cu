@@ -134,7 +134,7 @@ int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg_in) {
   } while (0)
 
   MS_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
-  if (cfg.stream) {
+  if (cfg.stream || cfg.use_stream) {
     c->stream = (cudaStream_t)cfg.stream;
   } else {
     MS_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
@@ -350,8 +350,9 @@ int ms_crypt_host(ms_ctx *c, int op, void *host_base, uint64_t first_page_id, si
         c->hs_buf[i] = nullptr;
       }
     }
-    c->hs_cap = 0;
+    c->hs_cap = chunk_bytes;
   }
+  // every per-stream buffer holds hs_cap >= chunk_bytes bytes
   for (int i = 0; i < n_streams; ++i) {
     if (!c->hs[i]) {
       e = cudaStreamCreateWithFlags(&c->hs[i], cudaStreamNonBlocking);
@@ -360,11 +361,10 @@ int ms_crypt_host(ms_ctx *c, int op, void *host_base, uint64_t first_page_id, si
       if (e != cudaSuccess) return cuda_fail(c, e);
     }
     if (!c->hs_buf[i]) {
-      e = cudaMalloc(&c->hs_buf[i], chunk_bytes);
+      e = cudaMalloc(&c->hs_buf[i], c->hs_cap);
       if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MS_ENOMEM : cuda_fail(c, e);
     }
   }
-  c->hs_cap = std::max(c->hs_cap, chunk_bytes);
   // order after earlier work on the context stream
   e = cudaEventRecord(c->sync_ev, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);

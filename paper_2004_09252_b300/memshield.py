@@ -42,6 +42,7 @@ class ms_config(ctypes.Structure):
         ("threads_per_cta", ctypes.c_uint32),
         ("dr_unroll", ctypes.c_uint32),
         ("check_duplicates", ctypes.c_uint32),
+        ("use_stream", ctypes.c_uint32),
     ]
 
 
@@ -137,7 +138,9 @@ class Context:
         cfg = config_default()
         cfg.device = device
         if stream is not None:
+            # an explicit stream, including handle 0 (the legacy default stream)
             cfg.stream = stream if isinstance(stream, int) else stream.cuda_stream
+            cfg.use_stream = 1
         cfg.domain = domain
         cfg.rounds = rounds
         if list_capacity:

