@@ -178,6 +178,34 @@ int ms_last_cuda_error(const ms_ctx *ctx);
 int ms_crypt_host(ms_ctx *ctx, int op, void *host_base, uint64_t first_page_id, size_t n_pages,
                   size_t chunk_bytes, int n_streams);
 
+/*
+ * Allocation-free variant of ms_encrypt_pages / ms_decrypt_pages.  The paper
+ * has no counterpart: this is a library convenience.
+ *
+ * For callers that must not call cudaMalloc at the moment they encrypt or
+ * decrypt -- typically code resolving a page fault, where an allocation can
+ * stall the whole device, can fail because a caching allocator holds the free
+ * memory, and is forbidden while the caller's stream is being captured.  The
+ * context (created earlier by ms_init, which does allocate) supplies the key,
+ * the stream and the launch shape; the call itself allocates nothing.
+ *
+ * pages: host list of n entries, checked like ms_encrypt_pages (MS_EINVAL on a
+ * NULL or misaligned address, nothing launched).  n above
+ * MS_NOALLOC_MAX_PAGES returns MS_ERANGE and does nothing.
+ * Scratch: the entry list and the status word go to one file-scope device
+ * array of 256 + 16 * MS_NOALLOC_MAX_PAGES bytes (256.25 KiB) that every GPU
+ * using the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (set-up, once per device); make
+ * that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU (two contexts, two threads, two
+ * streams) race on it and must be serialised by the caller.
+ * Unlike ms_encrypt_pages, the call waits (bounded by timeout_ms) for the
+ * kernel to finish and returns its status: MS_OK, MS_EINVAL for a bad entry,
+ * MS_ETIMEDOUT, MS_ECUDA.
+ */
+#define MS_NOALLOC_MAX_PAGES 16384u
+int ms_crypt_pages_noalloc(ms_ctx *ctx, int op, const ms_page *pages, size_t n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,7 @@ MS_BLOCKS_PER_PAGE = 64
 MS_KEY_BYTES = 32
 MS_OK, MS_EINVAL, MS_ENOTINIT, MS_ENOMEM, MS_ECUDA, MS_ETIMEDOUT, MS_EBUSY, MS_ERANGE = 0, -1, -2, -3, -4, -5, -6, -7
 MS_ENCRYPT, MS_DECRYPT = 0, 1
+MS_NOALLOC_MAX_PAGES = 16384
 
 PAGE_DTYPE = np.dtype([("addr", "<u8"), ("page_id", "<u8")])
 
@@ -80,6 +81,7 @@ def _load():
         "ms_crypt_host": (I, [P, I, P, U64, S, S, I]),
         "ms_get_shape": (I, [P, ctypes.POINTER(ms_shape)]),
         "ms_set_shape": (I, [P, ctypes.POINTER(ms_shape)]),
+        "ms_crypt_pages_noalloc": (I, [P, I, P, S]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -185,6 +187,12 @@ class Context:
                    n_streams: int = 0) -> None:
         _check(_lib.ms_crypt_host(self.handle, op, _ptr(host_base), first_page_id, n_pages, chunk_bytes,
                                   n_streams), "ms_crypt_host")
+
+    def crypt_pages_noalloc(self, op: int, pages: np.ndarray) -> None:
+        """Same transform as encrypt_pages, with no allocation in the call (waits for completion)."""
+        pages = np.ascontiguousarray(pages, dtype=PAGE_DTYPE)
+        _check(_lib.ms_crypt_pages_noalloc(self.handle, op, pages.ctypes.data, pages.size),
+               "ms_crypt_pages_noalloc")
 
     def get_shape(self) -> dict:
         sh = ms_shape()
