@@ -144,8 +144,11 @@ int ms_shutdown(ms_ctx *ctx);
  *   threads_per_cta    128, 256 or 512
  *   dr_unroll          double rounds per loop trip (1, 2, or all of them)
  *   rot_policy         0: rotations as funnel shifts; 1: rotations by 16 and 8
- *                      as byte permutes; 2: as 1, with 12 and 7 done on the
- *                      integer multiply pipe (x * 2^k, high + low halves)
+ *                      as byte permutes; 2..7: as 1, with some rotations by 12
+ *                      and 7 done on the integer multiply pipe (x * 2^k, high
+ *                      + low halves): 2 all of them, 3 the 7s, 4 the 12s,
+ *                      5 the 7s of column rounds, 6 the 7s through one wide
+ *                      multiply, 7 the 12s and 7s of column rounds
  * ms_set_shape returns MS_EINVAL (and changes nothing) for a shape that is
  * not compiled for the context's round count.
  */

@@ -27,13 +27,23 @@ constexpr uint32_t kSigma3 = 0x6b206574u;  // "te k"
 constexpr unsigned kStatusBadEntry = 1u;   // a device-side entry check failed
 
 // Rotation policies.  All compute the same left rotation; they differ in the
-// execution pipe the instruction lands on.
-//   kRotFunnel: every rotation is a funnel shift.
-//   kRotPerm:   rotations by 16 and 8 are byte permutes, 12 and 7 funnel shifts.
-//   kRotMul:    16 and 8 byte permutes; 12 and 7 as hi/lo halves of a 32x32
-//               multiply by 2^k (the multiplier comes from a kernel argument so
-//               it stays a real multiply) -- this moves work to the multiply pipe.
-enum RotPolicy { kRotFunnel = 0, kRotPerm = 1, kRotMul = 2 };
+// execution pipe each rotation lands on.  LOP3 (xor), funnel shifts and byte
+// permutes share the integer ALU pipe, which bounds this kernel; adds already
+// go to the multiply-add pipe, so the policies move some rotations there.
+//   kRotFunnel  every rotation is a funnel shift
+//   kRotPerm    rotations by 16 and 8 are byte permutes, 12 and 7 funnel shifts
+//   kRotMul     as kRotPerm, 12 and 7 as (x * 2^k).hi + (x * 2^k).lo
+//   kRotMul7    as kRotPerm, only the rotations by 7 through the multiplier
+//   kRotMul12   as kRotPerm, only the rotations by 12 through the multiplier
+//   kRotMul7Col as kRotPerm, rotations by 7 of the column rounds only
+//   kRotWide7   as kRotMul7, with one 32x32->64 multiply and an add
+//   kRotMulCol  as kRotPerm, rotations by 12 and 7 of the column rounds only
+// The multipliers 2^k come from a kernel argument, so the compiler keeps them
+// as real multiplies instead of folding them back into shifts.
+enum RotPolicy {
+  kRotFunnel = 0, kRotPerm = 1, kRotMul = 2, kRotMul7 = 3, kRotMul12 = 4,
+  kRotMul7Col = 5, kRotWide7 = 6, kRotMulCol = 7
+};
 
 struct MulConsts {
   uint32_t m12;  // 1 << 12
@@ -66,25 +76,34 @@ __device__ __forceinline__ uint32_t rotl_mul(uint32_t x, uint32_t m) {
   return r;
 }
 
-template <int POL>
+__device__ __forceinline__ uint32_t rotl_wide(uint32_t x, uint32_t m) {
+  uint64_t p;
+  asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(x), "r"(m));
+  return (uint32_t)p + (uint32_t)(p >> 32);
+}
+
+template <int POL, bool COL>
 __device__ __forceinline__ uint32_t rotl12(uint32_t x, const MulConsts &mc) {
-  if (POL == kRotMul) return rotl_mul(x, mc.m12);
+  if (POL == kRotMul || POL == kRotMul12 || (POL == kRotMulCol && COL)) return rotl_mul(x, mc.m12);
   return rotl_funnel<12>(x);
 }
 
-template <int POL>
+template <int POL, bool COL>
 __device__ __forceinline__ uint32_t rotl7(uint32_t x, const MulConsts &mc) {
-  if (POL == kRotMul) return rotl_mul(x, mc.m7);
+  if (POL == kRotMul || POL == kRotMul7 || ((POL == kRotMul7Col || POL == kRotMulCol) && COL))
+    return rotl_mul(x, mc.m7);
+  if (POL == kRotWide7) return rotl_wide(x, mc.m7);
   return rotl_funnel<7>(x);
 }
 
-template <int POL>
+// COL: the quarter round belongs to a column round (else a diagonal round).
+template <int POL, bool COL>
 __device__ __forceinline__ void quarter_round(uint32_t &a, uint32_t &b, uint32_t &c, uint32_t &d,
                                               const MulConsts &mc) {
   a += b; d = rotl16<POL>(d ^ a);
-  c += d; b = rotl12<POL>(b ^ c, mc);
+  c += d; b = rotl12<POL, COL>(b ^ c, mc);
   a += b; d = rotl8<POL>(d ^ a);
-  c += d; b = rotl7<POL>(b ^ c, mc);
+  c += d; b = rotl7<POL, COL>(b ^ c, mc);
 }
 
 // Key words 0..7 and the per-page nonce words (13, 14, 15).
@@ -118,15 +137,15 @@ __device__ __forceinline__ void xor_block(uint4 *__restrict__ dst, const BlockSe
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
       // column round
-      quarter_round<POL>(x0, x4, x8, x12, mc);
-      quarter_round<POL>(x1, x5, x9, x13, mc);
-      quarter_round<POL>(x2, x6, x10, x14, mc);
-      quarter_round<POL>(x3, x7, x11, x15, mc);
+      quarter_round<POL, true>(x0, x4, x8, x12, mc);
+      quarter_round<POL, true>(x1, x5, x9, x13, mc);
+      quarter_round<POL, true>(x2, x6, x10, x14, mc);
+      quarter_round<POL, true>(x3, x7, x11, x15, mc);
       // diagonal round
-      quarter_round<POL>(x0, x5, x10, x15, mc);
-      quarter_round<POL>(x1, x6, x11, x12, mc);
-      quarter_round<POL>(x2, x7, x8, x13, mc);
-      quarter_round<POL>(x3, x4, x9, x14, mc);
+      quarter_round<POL, false>(x0, x5, x10, x15, mc);
+      quarter_round<POL, false>(x1, x6, x11, x12, mc);
+      quarter_round<POL, false>(x2, x7, x8, x13, mc);
+      quarter_round<POL, false>(x3, x4, x9, x14, mc);
     }
   }
 

@@ -34,6 +34,12 @@ const Entry kTable[] = {
     MS_K1(20, 2, 2, 2), MS_K1(20, 2, 10, 2),
     MS_K1(20, 4, 2, 1), MS_K1(20, 4, 10, 1),
     MS_K1(20, 4, 2, 2), MS_K1(20, 4, 10, 2),
+    // finer moves of rotations onto the multiply pipe
+    MS_K1(20, 1, 10, 3), MS_K1(20, 2, 10, 3), MS_K1(20, 4, 10, 3), MS_K1(20, 1, 2, 3),
+    MS_K1(20, 1, 10, 4), MS_K1(20, 2, 10, 4), MS_K1(20, 4, 10, 4),
+    MS_K1(20, 1, 10, 5), MS_K1(20, 2, 10, 5), MS_K1(20, 4, 10, 5),
+    MS_K1(20, 1, 10, 6), MS_K1(20, 2, 10, 6), MS_K1(20, 4, 10, 6),
+    MS_K1(20, 1, 10, 7), MS_K1(20, 2, 10, 7), MS_K1(20, 4, 10, 7),
     // Reduced-round variants.
     MS_K1(12, 1, 6, 1), MS_K1(12, 2, 6, 1), MS_K1(12, 1, 2, 1),
     MS_K1(8, 1, 4, 1), MS_K1(8, 2, 4, 1), MS_K1(8, 1, 2, 1),

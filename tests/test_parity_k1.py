@@ -47,7 +47,10 @@ def test_small_config_encrypt_then_decrypt(ms, key1):
 SHAPES = [(b, u, p) for (b, u, p) in [
     (1, 1, 0), (1, 2, 0), (1, 10, 0), (1, 1, 1), (1, 2, 1), (1, 10, 1), (1, 1, 2), (1, 2, 2), (1, 10, 2),
     (2, 2, 0), (2, 10, 0), (2, 2, 1), (2, 10, 1), (2, 2, 2), (2, 10, 2),
-    (4, 2, 1), (4, 10, 1), (4, 2, 2), (4, 10, 2)]]
+    (4, 2, 1), (4, 10, 1), (4, 2, 2), (4, 10, 2),
+    (1, 10, 3), (2, 10, 3), (4, 10, 3), (1, 2, 3), (1, 10, 4), (2, 10, 4), (4, 10, 4),
+    (1, 10, 5), (2, 10, 5), (4, 10, 5), (1, 10, 6), (2, 10, 6), (4, 10, 6),
+    (1, 10, 7), (2, 10, 7), (4, 10, 7)]]
 
 
 @pytest.mark.parametrize("bpt,unr,pol", SHAPES)
