@@ -182,6 +182,84 @@ int ms_crypt_host(ms_ctx *ctx, int op, void *host_base, uint64_t first_page_id, 
                   size_t chunk_bytes, int n_streams);
 
 /*
+ * ---- Batched form (persistent kernel fed by a device work queue) ----
+ *
+ * Sec. 4.4: the GPU module's workers take pages from queues that many host
+ * threads fill, so uneven lists of pages (from faults and evictions) share
+ * the GPU.  Here requests are appended to a host queue buffer; a submit
+ * copies it into a device work queue and launches one persistent grid
+ * (sized to what fits on the GPU) whose CTAs claim `grab` pages at a time
+ * with an atomic on the queue head until the queue is empty.  The launch is
+ * a captured CUDA graph (head reset, then the kernel) unless use_graph is 0.
+ * Two queue buffers alternate, so requests for the next batch can be added
+ * while the previous one runs.
+ *
+ * Ownership: page memory stays the caller's and must stay valid until
+ * ms_sync(ctx) returns after the submit; entries are copied by
+ * ms_batch_add.  A page must not appear twice in one batch.  Destroy every
+ * batch before ms_shutdown of its context.
+ */
+typedef struct ms_batch ms_batch;
+
+#define MS_BATCH_MAX_CAPACITY (1u << 26)
+
+typedef struct ms_batch_config {
+  uint32_t capacity;     /* pages per batch (default 1 << 20, max MS_BATCH_MAX_CAPACITY) */
+  uint32_t use_graph;    /* nonzero (default): launch through a captured CUDA graph */
+  uint32_t grab;         /* pages a CTA claims per atomic; 0 = the context's tuned value */
+  uint32_t ctas_per_sm;  /* persistent CTAs per SM; 0 = the tuned value (all that fit) */
+} ms_batch_config;
+
+typedef struct ms_batch_stats {
+  uint64_t requests;       /* successful ms_batch_add calls */
+  uint64_t pages;          /* pages added */
+  uint64_t submits;        /* non-empty submits */
+  uint64_t graph_launches; /* submits that launched the captured graph */
+} ms_batch_stats;
+
+void ms_batch_config_default(ms_batch_config *cfg);
+/* Allocates two pinned + two device queue buffers of 256 + 16 * capacity bytes. */
+int ms_batch_create(ms_ctx *ctx, const ms_batch_config *cfg, ms_batch **out);
+/* Append one request (op is bookkeeping: encryption = decryption).  Entries are
+ * checked on the host (MS_EINVAL).  MS_EBUSY: the batch is full, submit first. */
+int ms_batch_add(ms_batch *batch, int op, const ms_page *pages, size_t n);
+/* Append n_requests requests at once: request r is op ops[r] on
+ * pages[offsets[r] .. offsets[r + 1]) (offsets has n_requests + 1 entries).
+ * Stops at the first request that fails (MS_EBUSY when the batch is full);
+ * *added (may be NULL) receives the number of requests queued. */
+int ms_batch_add_requests(ms_batch *batch, size_t n_requests, const int *ops, const uint64_t *offsets,
+                          const ms_page *pages, size_t *added);
+/* Copy the queued requests to the device and launch K2; asynchronous (ms_sync). */
+int ms_batch_submit(ms_batch *batch);
+int ms_batch_get_stats(const ms_batch *batch, ms_batch_stats *out);
+/* Waits (bounded) for the batch's work, then frees it.  NULL is a no-op. */
+int ms_batch_destroy(ms_batch *batch);
+
+/*
+ * ---- Autotuner ----
+ * Times every compiled K1 shape (blocks per thread, threads per CTA, unroll,
+ * rotation policy) on sample_pages contiguous pages (0 = 65536, 256 MiB), then
+ * K2's pages-per-claim (1..64) and CTAs per SM (all that fit, or half) on a
+ * scattered list of the same pages, and makes the fastest the context's
+ * shape.  It allocates (and frees) its own sample buffer; page contents do
+ * not matter.  Takes seconds; call it once after ms_init.
+ */
+typedef struct ms_tune_result {
+  ms_shape shape;        /* chosen K1 shape */
+  double k1_gbs;         /* its throughput on the sample, page bytes per second / 1e9 */
+  uint32_t grab;         /* chosen K2 pages per claim */
+  uint32_t ctas_per_sm;  /* chosen K2 CTAs per SM */
+  double queue_gbs;      /* K2 throughput on the scattered sample */
+  uint32_t tried;        /* configurations timed */
+} ms_tune_result;
+
+int ms_autotune(ms_ctx *ctx, size_t sample_pages, ms_tune_result *out);
+/* One-line text table: GPU name, SM count, rounds, K1 shape, K2 grab and CTAs/SM.
+ * Load rejects (MS_EINVAL) a table made for another GPU or round count. */
+int ms_tune_save(const ms_ctx *ctx, const char *path);
+int ms_tune_load(ms_ctx *ctx, const char *path);
+
+/*
  * Allocation-free variant of ms_encrypt_pages / ms_decrypt_pages.  The paper
  * has no counterpart: this is a library convenience.
  *

@@ -1,0 +1,245 @@
+// Batched form: requests (uneven page lists, as faults and evictions produce
+// them) are appended to a host-side queue buffer; a submit copies the buffer
+// to the device work queue and launches the persistent kernel K2 through a
+// captured CUDA graph (memset of the queue head, then K2).  Two queue buffers
+// alternate, so the host fills one while the GPU drains the other.
+//
+// Paper counterpart (Sec. 4.4): the GPU module's workers take pages from
+// queues that many host threads fill; here one device queue per batch feeds
+// every CTA of a persistent grid, and the grid ends when the queue is empty.
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "ms_internal.h"
+
+namespace {
+
+constexpr size_t kHeader = 256;       // queue buffer: [count @0][head @128][items @256]
+constexpr size_t kHeadOffset = 128;
+
+struct QBuf {
+  uint8_t *h = nullptr;  // pinned host copy (header + items)
+  uint8_t *d = nullptr;  // device work queue
+  size_t n = 0;          // items queued
+  cudaEvent_t done = nullptr;
+  bool inflight = false;
+  cudaGraphExec_t exec = nullptr;
+  unsigned exec_key = ~0u;  // tune generation the graph was captured for
+};
+
+}  // namespace
+
+struct ms_batch {
+  ms_ctx *ctx = nullptr;
+  ms_batch_config cfg{};
+  QBuf buf[2];
+  int cur = 0;
+  std::mutex mu;
+  ms_batch_stats stats{};
+};
+
+using namespace ms;
+
+namespace {
+
+int free_batch(ms_batch *b) {
+  int rc = MS_OK;
+  for (QBuf &q : b->buf) {
+    if (q.inflight && q.done) {
+      int r = wait_event(b->ctx, q.done, b->ctx->cfg.timeout_ms);
+      if (r != MS_OK && rc == MS_OK) rc = r;
+    }
+    if (q.exec) cudaGraphExecDestroy(q.exec);
+    if (q.done) cudaEventDestroy(q.done);
+    if (q.h) cudaFreeHost(q.h);
+    if (q.d) cudaFree(q.d);
+  }
+  delete b;
+  return rc;
+}
+
+// The K2 launch parameters of this batch (config overrides, else the context's tuning).
+void batch_params(const ms_batch *b, QueueKernel *k, int *grid, int *grab) {
+  const ms_ctx *c = b->ctx;
+  queue_kernel((int)c->cfg.rounds, c->tune, k);
+  const int cps = b->cfg.ctas_per_sm ? (int)b->cfg.ctas_per_sm : c->qtune.ctas_per_sm;
+  *grid = queue_grid(c, *k, c->tune.tpc, cps);
+  *grab = b->cfg.grab ? (int)b->cfg.grab : c->qtune.grab;
+}
+
+QueueArgs queue_args(const ms_batch *b, const QBuf &q, int grab) {
+  const ms_ctx *c = b->ctx;
+  QueueArgs a{};
+  a.items = reinterpret_cast<const ms_page *>(q.d + kHeader);
+  a.count = reinterpret_cast<const uint32_t *>(q.d);
+  a.head = reinterpret_cast<uint32_t *>(q.d + kHeadOffset);
+  a.grab = (uint32_t)grab;
+  a.key = c->d_key;
+  a.domain = c->cfg.domain;
+  a.status = c->d_status;
+  a.mc.m12 = 1u << 12;
+  a.mc.m7 = 1u << 7;
+  return a;
+}
+
+// (Re)capture the graph of queue buffer q: head := 0, then K2 over the queue.
+cudaError_t capture(ms_batch *b, QBuf &q) {
+  QueueKernel k;
+  int grid, grab;
+  batch_params(b, &k, &grid, &grab);
+  const QueueArgs a = queue_args(b, q, grab);
+  cudaStream_t cs;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = cudaMemsetAsync(q.d + kHeadOffset, 0, sizeof(uint32_t), cs);
+    cudaError_t e2 = (e1 == cudaSuccess) ? k.launch(a, grid, b->ctx->tune.tpc, cs) : e1;
+    e = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) {
+    if (q.exec) {
+      cudaGraphExecDestroy(q.exec);
+      q.exec = nullptr;
+    }
+    e = cudaGraphInstantiate(&q.exec, g, 0);
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e == cudaSuccess) q.exec_key = b->ctx->tune_gen.load();
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ms_batch_config_default(ms_batch_config *cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->capacity = 1u << 20;
+  cfg->use_graph = 1;
+}
+
+int ms_batch_create(ms_ctx *c, const ms_batch_config *cfg_in, ms_batch **out) {
+  if (!out) return MS_EINVAL;
+  *out = nullptr;
+  if (!c || !c->alive) return MS_ENOTINIT;
+  ms_batch_config cfg;
+  if (cfg_in) cfg = *cfg_in; else ms_batch_config_default(&cfg);
+  if (cfg.capacity == 0) cfg.capacity = 1u << 20;
+  if (cfg.capacity > MS_BATCH_MAX_CAPACITY) return MS_ERANGE;
+  if (cfg.grab > 4096) return MS_EINVAL;
+  QueueKernel k;
+  if (!queue_kernel((int)c->cfg.rounds, c->tune, &k)) return MS_EINVAL;
+  ms_batch *b = new (std::nothrow) ms_batch();
+  if (!b) return MS_ENOMEM;
+  b->ctx = c;
+  b->cfg = cfg;
+  DeviceGuard g(c->device);
+  const size_t bytes = kHeader + sizeof(ms_page) * (size_t)cfg.capacity;
+  for (QBuf &q : b->buf) {
+    cudaError_t e = cudaHostAlloc(&q.h, bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc(&q.d, bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      free_batch(b);
+      return e == cudaErrorMemoryAllocation ? MS_ENOMEM : cuda_fail(c, e);
+    }
+    std::memset(q.h, 0, kHeader);
+  }
+  *out = b;
+  return MS_OK;
+}
+
+int ms_batch_add(ms_batch *b, int op, const ms_page *pages, size_t n) {
+  if (!b) return MS_EINVAL;
+  ms_ctx *c = b->ctx;
+  if (!c || !c->alive) return MS_ENOTINIT;
+  if (op != MS_ENCRYPT && op != MS_DECRYPT) return MS_EINVAL;
+  if (n == 0) return MS_OK;
+  if (!pages) return MS_EINVAL;
+  for (size_t i = 0; i < n; ++i)
+    if (pages[i].addr == 0 || (pages[i].addr & 15u)) return MS_EINVAL;
+  std::lock_guard<std::mutex> lk(b->mu);
+  QBuf &q = b->buf[b->cur];
+  if (q.n + n > b->cfg.capacity) return MS_EBUSY;  // submit first
+  if (q.inflight) {  // the GPU may still read this buffer's previous batch
+    DeviceGuard g(c->device);
+    int rc = wait_event(c, q.done, c->cfg.timeout_ms);
+    if (rc != MS_OK) return rc;
+    q.inflight = false;
+  }
+  std::memcpy(q.h + kHeader + sizeof(ms_page) * q.n, pages, n * sizeof(ms_page));
+  q.n += n;
+  b->stats.requests += 1;
+  b->stats.pages += n;
+  return MS_OK;
+}
+
+int ms_batch_add_requests(ms_batch *b, size_t n_requests, const int *ops, const uint64_t *offsets,
+                          const ms_page *pages, size_t *added) {
+  if (added) *added = 0;
+  if (!b || (n_requests && (!ops || !offsets || !pages))) return MS_EINVAL;
+  size_t r = 0;
+  for (; r < n_requests; ++r) {
+    if (offsets[r + 1] < offsets[r]) return MS_EINVAL;
+    const int rc = ms_batch_add(b, ops[r], pages + offsets[r], (size_t)(offsets[r + 1] - offsets[r]));
+    if (rc != MS_OK) return rc;
+    if (added) *added = r + 1;
+  }
+  return MS_OK;
+}
+
+int ms_batch_submit(ms_batch *b) {
+  if (!b) return MS_EINVAL;
+  ms_ctx *c = b->ctx;
+  if (!c || !c->alive) return MS_ENOTINIT;
+  std::lock_guard<std::mutex> lk(b->mu);
+  QBuf &q = b->buf[b->cur];
+  if (q.n == 0) return MS_OK;
+  std::lock_guard<std::mutex> lk2(c->mu);
+  DeviceGuard g(c->device);
+  const uint32_t count = (uint32_t)q.n;
+  std::memcpy(q.h, &count, sizeof(count));
+  cudaError_t e = cudaMemcpyAsync(q.d, q.h, kHeader + sizeof(ms_page) * q.n, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  if (b->cfg.use_graph) {
+    if (!q.exec || q.exec_key != c->tune_gen.load()) {
+      e = capture(b, q);
+      if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    e = cudaGraphLaunch(q.exec, c->stream);
+    b->stats.graph_launches += 1;
+  } else {
+    QueueKernel k;
+    int grid, grab;
+    batch_params(b, &k, &grid, &grab);
+    e = cudaMemsetAsync(q.d + kHeadOffset, 0, sizeof(uint32_t), c->stream);
+    if (e == cudaSuccess) e = k.launch(queue_args(b, q, grab), grid, c->tune.tpc, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(q.done, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  q.inflight = true;
+  q.n = 0;
+  b->stats.submits += 1;
+  b->cur ^= 1;
+  return MS_OK;
+}
+
+int ms_batch_get_stats(const ms_batch *b, ms_batch_stats *out) {
+  if (!b || !out) return MS_EINVAL;
+  *out = b->stats;
+  return MS_OK;
+}
+
+int ms_batch_destroy(ms_batch *b) {
+  if (!b) return MS_OK;
+  DeviceGuard g(b->ctx->device);
+  return free_batch(b);
+}
+
+}  // extern "C"

@@ -209,4 +209,58 @@ __global__ void __launch_bounds__(512) k_pages(const PageArgs a) {
   }
 }
 
+// Arguments of the persistent queue kernel.
+struct QueueArgs {
+  const ms_page *items;   // the device work queue: one entry per page
+  const uint32_t *count;  // number of valid entries (device word written with the items)
+  uint32_t *head;         // next unclaimed entry; 0 at launch
+  uint32_t grab;          // pages a CTA claims per atomic on head
+  const uint4 *key;
+  uint32_t domain;
+  unsigned int *status;
+  MulConsts mc;
+};
+
+// K2, the persistent batched kernel.  A grid sized to the resident capacity
+// of the GPU drains the work queue: each CTA claims `grab` consecutive entries
+// with one atomic on the queue head and processes them blockDim / TPP pages at a
+// time (TPP = 64 / BPT threads per page), until the head passes the count.
+// The head only grows, so every CTA leaves after at most count / grab + 1
+// claims; nothing waits.
+template <int ROUNDS, int BPT, int UNR, int POL>
+__global__ void __launch_bounds__(512) k_queue(const QueueArgs q) {
+  constexpr uint32_t TPP = 64 / BPT;
+  __shared__ uint32_t s_base;
+  const uint32_t n = *q.count;
+  const uint32_t pages_per_pass = blockDim.x / TPP;
+  const uint32_t lp = threadIdx.x / TPP;  // page slot of this thread within a pass
+  const uint32_t t = threadIdx.x % TPP;
+  BlockSeed s;
+  load_key(q.key, s.k);
+  s.n2 = q.domain;
+  for (;;) {
+    if (threadIdx.x == 0) s_base = atomicAdd(q.head, q.grab);
+    __syncthreads();
+    const uint32_t base = s_base;
+    __syncthreads();
+    if (base >= n) break;
+    const uint32_t end = min(base + q.grab, n);
+    for (uint32_t p = base + lp; p < end; p += pages_per_pass) {
+      const ms_page e = q.items[p];
+      if (!entry_ok(e.addr)) {
+        if (t == 0) atomicOr(q.status, kStatusBadEntry);
+        continue;
+      }
+      s.n0 = (uint32_t)e.page_id;
+      s.n1 = (uint32_t)(e.page_id >> 32);
+      uint4 *pg = reinterpret_cast<uint4 *>(e.addr);
+#pragma unroll 1
+      for (int b = 0; b < BPT; ++b) {
+        const uint32_t j = t + b * TPP;
+        xor_block<ROUNDS, UNR, POL>(pg + 4 * j, s, j, q.mc);
+      }
+    }
+  }
+}
+
 }  // namespace ms

@@ -325,6 +325,7 @@ int ms_set_shape(ms_ctx *c, const ms_shape *sh) {
   if (!shape_available((int)c->cfg.rounds, t)) return MS_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
   c->tune = t;
+  c->tune_gen.fetch_add(1);
   return MS_OK;
 }
 

@@ -21,6 +21,12 @@ struct Tune {
   int pol = kRotPerm;
 };
 
+// Launch parameters of the persistent queue kernel (K2).
+struct QTune {
+  int grab = 8;         // pages a CTA claims per atomic on the queue head
+  int ctas_per_sm = 0;  // 0 = as many as fit (occupancy)
+};
+
 constexpr int kListSlots = 4;
 constexpr int kMaxHostStreams = 4;
 
@@ -44,6 +50,8 @@ struct ms_ctx {
   unsigned int *h_status = nullptr;  // pinned landing word for ms_sync
   cudaEvent_t sync_ev = nullptr;
   ms::Tune tune;
+  ms::QTune qtune;
+  std::atomic<unsigned> tune_gen{0};  // bumped whenever tune/qtune change
   ms::ListSlot slots[ms::kListSlots];
   int next_slot = 0;
   // host streaming (ms_crypt_host)
@@ -82,5 +90,17 @@ cudaError_t launch_pages(const ms_ctx *c, const PageArgs &a, cudaStream_t s);
 cudaError_t launch_pages_shape(const PageArgs &a, int rounds, const Tune &t, bool range,
                                cudaStream_t s);
 bool shape_available(int rounds, const Tune &t);
+int k1_shape_count();
+void k1_shape(int i, int *rounds, Tune *t);
+
+// K2: the persistent queue kernel.  `t` picks the instance (the nearest
+// compiled one when t itself is not compiled for K2).
+struct QueueKernel {
+  const void *fn = nullptr;  // kernel symbol, for occupancy queries and graph capture
+  cudaError_t (*launch)(const QueueArgs &, int grid, int tpc, cudaStream_t) = nullptr;
+  Tune shape;                // the instance actually used
+};
+bool queue_kernel(int rounds, const Tune &t, QueueKernel *out);
+int queue_grid(const ms_ctx *c, const QueueKernel &k, int tpc, int ctas_per_sm);
 
 }  // namespace ms

@@ -56,6 +56,35 @@ class ms_shape(ctypes.Structure):
     ]
 
 
+class ms_batch_config(ctypes.Structure):
+    _fields_ = [
+        ("capacity", ctypes.c_uint32),
+        ("use_graph", ctypes.c_uint32),
+        ("grab", ctypes.c_uint32),
+        ("ctas_per_sm", ctypes.c_uint32),
+    ]
+
+
+class ms_batch_stats(ctypes.Structure):
+    _fields_ = [
+        ("requests", ctypes.c_uint64),
+        ("pages", ctypes.c_uint64),
+        ("submits", ctypes.c_uint64),
+        ("graph_launches", ctypes.c_uint64),
+    ]
+
+
+class ms_tune_result(ctypes.Structure):
+    _fields_ = [
+        ("shape", ms_shape),
+        ("k1_gbs", ctypes.c_double),
+        ("grab", ctypes.c_uint32),
+        ("ctas_per_sm", ctypes.c_uint32),
+        ("queue_gbs", ctypes.c_double),
+        ("tried", ctypes.c_uint32),
+    ]
+
+
 def _load():
     path = _build.LIB
     if not os.path.exists(path):
@@ -82,6 +111,16 @@ def _load():
         "ms_get_shape": (I, [P, ctypes.POINTER(ms_shape)]),
         "ms_set_shape": (I, [P, ctypes.POINTER(ms_shape)]),
         "ms_crypt_pages_noalloc": (I, [P, I, P, S]),
+        "ms_batch_config_default": (None, [ctypes.POINTER(ms_batch_config)]),
+        "ms_batch_create": (I, [P, ctypes.POINTER(ms_batch_config), ctypes.POINTER(P)]),
+        "ms_batch_add": (I, [P, I, P, S]),
+        "ms_batch_submit": (I, [P]),
+        "ms_batch_add_requests": (I, [P, S, P, P, P, ctypes.POINTER(ctypes.c_size_t)]),
+        "ms_batch_get_stats": (I, [P, ctypes.POINTER(ms_batch_stats)]),
+        "ms_batch_destroy": (I, [P]),
+        "ms_autotune": (I, [P, S, ctypes.POINTER(ms_tune_result)]),
+        "ms_tune_save": (I, [P, ctypes.c_char_p]),
+        "ms_tune_load": (I, [P, ctypes.c_char_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -194,6 +233,21 @@ class Context:
         _check(_lib.ms_crypt_pages_noalloc(self.handle, op, pages.ctypes.data, pages.size),
                "ms_crypt_pages_noalloc")
 
+    def autotune(self, sample_pages: int = 0) -> dict:
+        r = ms_tune_result()
+        _check(_lib.ms_autotune(self.handle, sample_pages, ctypes.byref(r)), "ms_autotune")
+        return {"shape": {f: getattr(r.shape, f) for f, _ in ms_shape._fields_}, "k1_gbs": r.k1_gbs,
+                "grab": r.grab, "ctas_per_sm": r.ctas_per_sm, "queue_gbs": r.queue_gbs, "tried": r.tried}
+
+    def tune_save(self, path: str) -> None:
+        _check(_lib.ms_tune_save(self.handle, path.encode()), "ms_tune_save")
+
+    def tune_load(self, path: str) -> int:
+        return _lib.ms_tune_load(self.handle, path.encode())
+
+    def batch(self, capacity: int = 0, use_graph: bool = True, grab: int = 0, ctas_per_sm: int = 0) -> "Batch":
+        return Batch(self, capacity, use_graph, grab, ctas_per_sm)
+
     def get_shape(self) -> dict:
         sh = ms_shape()
         _check(_lib.ms_get_shape(self.handle, ctypes.byref(sh)), "ms_get_shape")
@@ -230,3 +284,65 @@ class Context:
             self.shutdown()
         except Exception:
             pass
+
+
+class Batch:
+    """An ms_batch: requests queued on the host, drained on the GPU by the persistent kernel."""
+
+    def __init__(self, ctx: Context, capacity: int = 0, use_graph: bool = True, grab: int = 0,
+                 ctas_per_sm: int = 0):
+        cfg = ms_batch_config()
+        _lib.ms_batch_config_default(ctypes.byref(cfg))
+        if capacity:
+            cfg.capacity = capacity
+        cfg.use_graph = 1 if use_graph else 0
+        cfg.grab = grab
+        cfg.ctas_per_sm = ctas_per_sm
+        h = ctypes.c_void_p()
+        _check(_lib.ms_batch_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "ms_batch_create")
+        self.handle = h.value
+        self.ctx = ctx
+
+    def add(self, op: int, pages: np.ndarray) -> int:
+        """Queue one request; returns the status code (MS_EBUSY when full) without raising for it."""
+        pages = np.ascontiguousarray(pages, dtype=PAGE_DTYPE)
+        rc = _lib.ms_batch_add(self.handle, op, pages.ctypes.data, pages.size)
+        if rc not in (MS_OK, MS_EBUSY):
+            raise MemShieldError(rc, "ms_batch_add")
+        return rc
+
+    def add_requests(self, ops: np.ndarray, offsets: np.ndarray, pages: np.ndarray, first: int = 0,
+                     count: int | None = None) -> tuple[int, int]:
+        """Queue requests first..first+count-1 of a request table; returns (status, queued)."""
+        ops = np.ascontiguousarray(ops, dtype=np.int32)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        pages = np.ascontiguousarray(pages, dtype=PAGE_DTYPE)
+        n = (len(ops) - first) if count is None else count
+        added = ctypes.c_size_t(0)
+        rc = _lib.ms_batch_add_requests(self.handle, n, ops.ctypes.data + 4 * first,
+                                        offsets.ctypes.data + 8 * first, pages.ctypes.data,
+                                        ctypes.byref(added))
+        if rc not in (MS_OK, MS_EBUSY):
+            raise MemShieldError(rc, "ms_batch_add_requests")
+        return rc, added.value
+
+    def submit(self) -> None:
+        _check(_lib.ms_batch_submit(self.handle), "ms_batch_submit")
+
+    def stats(self) -> dict:
+        st = ms_batch_stats()
+        _check(_lib.ms_batch_get_stats(self.handle, ctypes.byref(st)), "ms_batch_get_stats")
+        return {f: getattr(st, f) for f, _ in ms_batch_stats._fields_}
+
+    def destroy(self) -> int:
+        if self.handle:
+            rc = _lib.ms_batch_destroy(self.handle)
+            self.handle = None
+            return rc
+        return MS_OK
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()

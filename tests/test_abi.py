@@ -63,9 +63,11 @@ def test_struct_layout_matches_c():
     #include <stddef.h>
     #include "memshield.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu %zu\n", sizeof(ms_page), sizeof(ms_config),
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ms_page), sizeof(ms_config),
              offsetof(ms_config, stream), offsetof(ms_config, domain),
-             offsetof(ms_config, timeout_ms), offsetof(ms_config, use_stream));
+             offsetof(ms_config, timeout_ms), offsetof(ms_config, use_stream),
+             sizeof(ms_batch_config), sizeof(ms_batch_stats), sizeof(ms_tune_result),
+             offsetof(ms_tune_result, queue_gbs), offsetof(ms_tune_result, tried));
       return 0;
     }'''
     with tempfile.TemporaryDirectory() as d:
@@ -76,4 +78,6 @@ def test_struct_layout_matches_c():
         vals = [int(v) for v in subprocess.check_output([exe]).split()]
     cfg = m.ms_config
     assert vals == [m.PAGE_DTYPE.itemsize, ctypes.sizeof(cfg), cfg.stream.offset, cfg.domain.offset,
-                    cfg.timeout_ms.offset, cfg.use_stream.offset]
+                    cfg.timeout_ms.offset, cfg.use_stream.offset, ctypes.sizeof(m.ms_batch_config),
+                    ctypes.sizeof(m.ms_batch_stats), ctypes.sizeof(m.ms_tune_result),
+                    m.ms_tune_result.queue_gbs.offset, m.ms_tune_result.tried.offset]
