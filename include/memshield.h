@@ -260,6 +260,88 @@ int ms_tune_save(const ms_ctx *ctx, const char *path);
 int ms_tune_load(ms_ctx *ctx, const char *path);
 
 /*
+ * ---- Served form (continuous batching over host pages) ----
+ *
+ * Stands in for the paper's server + data thread (Sec. 4.2-4.4): faults ask
+ * for single pages to be decrypted, evictions hand over runs of pages to be
+ * encrypted, and both are served from a working set in host RAM.  A server
+ * thread admits requests in arrival order while the pinned staging budget
+ * has room and none of the request's pages is already in flight (a request
+ * touching an in-flight page waits for it, so results do not depend on the
+ * mix).  Admitted requests form a wave:
+ *   - worker threads copy its pages from the working set into pinned
+ *     staging (the paper's data thread copying into the shared page);
+ *   - the pages go host->device on one stream, through the page kernel and
+ *     back device->host on a second stream, so the copies of consecutive
+ *     waves overlap in both directions (double buffering, waves_in_flight);
+ *   - when a wave's copy-back completes, its pages are copied into the
+ *     working set, its staging is wiped if zero_staging is set (the paper
+ *     zeroes the shared page after each transfer), and its requests
+ *     complete.
+ * A new wave is formed as soon as the pipeline has room, from whatever has
+ * arrived: requests join while others are on the GPU (continuous batching).
+ * mode = MS_SERVE_ONE_PER_LAUNCH makes every wave a single request (the
+ * plain one-launch-per-request form, same machinery).
+ *
+ * The working set: n_pages pages of 4096 bytes at host_base (pinned memory
+ * is not required but avoids extra copies); page index i uses page id i.
+ * The caller must not touch a page while a request on it is pending.
+ */
+typedef struct ms_server ms_server;
+
+enum ms_serve_mode { MS_SERVE_CONTINUOUS = 0, MS_SERVE_ONE_PER_LAUNCH = 1 };
+
+typedef struct ms_server_config {
+  uint64_t staging_bytes;    /* admission budget in pinned staging (default 256 MiB, multiple of 4096) */
+  uint32_t max_wave_pages;   /* pages per wave at most (default staging pages / waves_in_flight) */
+  uint32_t waves_in_flight;  /* pipeline depth, 1..8 (default 2) */
+  uint32_t copy_threads;     /* gather/scatter worker threads, 0..32 (default 4) */
+  uint32_t max_pending;      /* tickets not yet completed-and-reaped, at most (default 1 << 20) */
+  uint32_t mode;             /* ms_serve_mode */
+  uint32_t zero_staging;     /* nonzero: wipe staging pages after each wave */
+  uint32_t max_request_pages;/* largest request accepted (default 4096; <= staging pages) */
+} ms_server_config;
+
+typedef struct ms_server_stats {
+  uint64_t requests_done;
+  uint64_t pages_done;
+  uint64_t waves;            /* kernel launches */
+  uint64_t max_wave_requests;
+  uint64_t max_wave_pages;
+  uint64_t conflict_waits;   /* times the head request waited for an in-flight page */
+  uint64_t budget_waits;     /* times the head request waited for staging room */
+} ms_server_stats;
+
+void ms_server_config_default(ms_server_config *cfg);
+/* Allocates the pinned staging, its device mirror and the entry lists, and
+ * starts the server thread and the copy workers. */
+int ms_server_create(ms_ctx *ctx, void *host_base, uint64_t n_pages, const ms_server_config *cfg,
+                     ms_server **out);
+/* Queue a request on pages page_index[0..n) of the working set (distinct
+ * within the request, each < n_pages); *ticket identifies it.  MS_ERANGE: n
+ * above max_request_pages; MS_EBUSY: max_pending tickets outstanding. */
+int ms_server_submit(ms_server *srv, int op, const uint64_t *page_index, uint32_t n, uint64_t *ticket);
+/* 1 = done (its pages are back in the working set), 0 = pending, < 0 = error. */
+int ms_server_poll(ms_server *srv, uint64_t ticket);
+/* Wait up to timeout_ms for the ticket: MS_OK, MS_ETIMEDOUT or an error. */
+int ms_server_wait(ms_server *srv, uint64_t ticket, uint32_t timeout_ms);
+/*
+ * Open-loop replay, for measurement: request r (op ops[r] on
+ * page_index[offsets[r] .. offsets[r + 1])) is submitted at arrival_s[r]
+ * seconds after the start, however far behind the server is, and
+ * latency_s[r] is its completion time minus that scheduled arrival (so
+ * queueing delay counts: no coordinated omission).  *makespan_s receives the
+ * time from the start to the last completion.  Waits at most timeout_ms
+ * after the last arrival for completions.
+ */
+int ms_server_replay(ms_server *srv, size_t n_requests, const double *arrival_s, const int *ops,
+                     const uint64_t *offsets, const uint64_t *page_index, double *latency_s,
+                     double *makespan_s, uint32_t timeout_ms);
+int ms_server_get_stats(const ms_server *srv, ms_server_stats *out);
+/* Drain (bounded), stop the threads and free.  NULL is a no-op. */
+int ms_server_destroy(ms_server *srv);
+
+/*
  * Allocation-free variant of ms_encrypt_pages / ms_decrypt_pages.  The paper
  * has no counterpart: this is a library convenience.
  *

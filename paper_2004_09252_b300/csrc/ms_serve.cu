@@ -1,0 +1,631 @@
+// Served form: continuous batching of encrypt / decrypt requests on pages of
+// a host working set, through pinned staging and a two-direction copy
+// pipeline.  Stands in for the paper's server + data thread (Sec. 4.2-4.4).
+//
+// Threads: callers submit requests (any thread); one server thread admits
+// them in arrival order, forms waves, gathers pages into pinned staging,
+// issues copies + kernel, and completes waves; a small pool of copy workers
+// shares the gather / scatter memcpys of large waves.
+//
+// Staging is a ring of S page slots (pinned host) mirrored on the device,
+// with one 16-byte kernel entry per slot.  A wave occupies a contiguous run
+// of slots; waves are freed in issue order.
+#include <sys/prctl.h>
+#include <time.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <functional>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "ms_internal.h"
+
+using namespace ms;
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+inline uint64_t now_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(clk::now().time_since_epoch()).count();
+}
+
+inline void nap_ns(long ns) {
+  struct timespec ts = {0, ns};
+  nanosleep(&ts, nullptr);
+}
+
+enum ReqState : int { kFree = 0, kQueued = 1, kAdmitted = 2, kDone = 3, kClaiming = 4 };
+
+struct Req {
+  std::atomic<int> state{kFree};
+  std::atomic<int> error{0};
+  std::atomic<uint64_t> ticket{~0ull};
+  int op = 0;
+  std::vector<uint64_t> pages;
+  uint64_t t_sched_ns = 0;     // arrival time latency is measured from
+  std::atomic<uint64_t> t_done_ns{0};
+  double *lat_out = nullptr;   // replay: where to write the latency, seconds
+};
+
+// Parallel-for over page indices for the gather / scatter memcpys.
+class CopyPool {
+ public:
+  explicit CopyPool(int n) {
+    for (int i = 0; i < n; ++i) th_.emplace_back([this] { worker(); });
+  }
+  ~CopyPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto &t : th_) t.join();
+  }
+  // Runs fn(i) for i in [0, n); the calling thread takes part.
+  void run(size_t n, const std::function<void(size_t)> &fn) {
+    if (th_.empty() || n < 64) {
+      for (size_t i = 0; i < n; ++i) fn(i);
+      return;
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      job_ = &fn;
+      n_ = n;
+      next_.store(0);
+      active_ = (int)th_.size();
+      ++gen_;
+    }
+    cv_.notify_all();
+    drain(fn, n);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [&] { return active_ == 0; });
+    job_ = nullptr;
+  }
+
+ private:
+  void drain(const std::function<void(size_t)> &fn, size_t n) {
+    for (;;) {
+      const size_t a = next_.fetch_add(16);
+      if (a >= n) break;
+      const size_t b = std::min(n, a + 16);
+      for (size_t i = a; i < b; ++i) fn(i);
+    }
+  }
+  void worker() {
+    uint64_t seen = 0;
+    for (;;) {
+      const std::function<void(size_t)> *job;
+      size_t n;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+        if (stop_) return;
+        seen = gen_;
+        job = job_;
+        n = n_;
+      }
+      drain(*job, n);
+      {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (--active_ == 0) done_cv_.notify_all();
+      }
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(size_t)> *job_ = nullptr;
+  size_t n_ = 0;
+  std::atomic<size_t> next_{0};
+  int active_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+
+struct Wave {
+  std::vector<uint64_t> tickets;
+  uint32_t pos = 0, len = 0, span = 0;  // first slot, pages, ring slots consumed (len + skipped tail)
+  cudaEvent_t ev_h2d = nullptr, ev_done = nullptr;
+};
+
+}  // namespace
+
+struct ms_server {
+  ms_ctx *ctx = nullptr;
+  uint8_t *host = nullptr;
+  uint64_t n_pages = 0;
+  ms_server_config cfg{};
+  uint32_t S = 0;  // staging slots
+  uint8_t *h_stage = nullptr, *d_stage = nullptr;
+  ms_page *h_ent = nullptr, *d_ent = nullptr;
+  cudaStream_t s_in = nullptr, s_work[2] = {nullptr, nullptr};
+  std::vector<Req> reqs;
+  std::mutex qmu;
+  std::condition_variable qcv;
+  std::deque<uint64_t> incoming;
+  std::atomic<uint64_t> next_ticket{0};
+  std::vector<uint8_t> busy;  // per working-set page: in a queued wave
+  uint32_t ring_head = 0, ring_used = 0;
+  std::deque<Wave> inflight;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  uint64_t wave_seq = 0;
+  std::thread th;
+  std::atomic<bool> stop{false};
+  std::atomic<bool> exited{false};
+  std::atomic<int> error{0};
+  CopyPool *pool = nullptr;
+  std::mutex done_mu;
+  std::condition_variable done_cv;
+  std::atomic<uint64_t> st_req{0}, st_pages{0}, st_waves{0}, st_maxreq{0}, st_maxpages{0}, st_conflict{0},
+      st_budget{0};
+
+  Req &slot(uint64_t t) { return reqs[t % reqs.size()]; }
+  void loop();
+  bool form_wave(Wave &w);
+  int issue(Wave &w);
+  void complete(Wave &w);
+  void fail_all(int code);
+};
+
+namespace {
+
+void atomic_max(std::atomic<uint64_t> &a, uint64_t v) {
+  uint64_t cur = a.load();
+  while (v > cur && !a.compare_exchange_weak(cur, v)) {
+  }
+}
+
+}  // namespace
+
+// Admission: take queued requests in arrival order while they fit.
+bool ms_server::form_wave(Wave &w) {
+  std::lock_guard<std::mutex> lk(qmu);
+  if (ring_used == 0) ring_head = 0;  // nothing in flight: the whole ring is free from slot 0
+  uint32_t pos = ring_head, waste = 0, len = 0;
+  size_t taken = 0;
+  for (uint64_t t : incoming) {
+    Req &r = slot(t);
+    const uint32_t n = (uint32_t)r.pages.size();
+    if (cfg.mode == MS_SERVE_ONE_PER_LAUNCH && taken == 1) break;
+    if (len + n > cfg.max_wave_pages && taken > 0) break;
+    // contiguous room in the ring: wrap to slot 0 if the tail is too short
+    uint32_t p = pos, wst = waste;
+    if (len == 0 && p + n > S) {
+      wst = S - p;
+      p = 0;
+    }
+    if (p + len + n > S || ring_used + wst + len + n > S) {
+      st_budget.fetch_add(1);
+      break;
+    }
+    bool conflict = false;
+    for (uint64_t pg : r.pages)
+      if (busy[pg]) {
+        conflict = true;
+        break;
+      }
+    if (conflict) {
+      st_conflict.fetch_add(1);
+      break;
+    }
+    for (uint64_t pg : r.pages) busy[pg] = 1;
+    pos = p;
+    waste = wst;
+    len += n;
+    w.tickets.push_back(t);
+    ++taken;
+  }
+  if (taken == 0) return false;
+  incoming.erase(incoming.begin(), incoming.begin() + (long)taken);
+  w.pos = pos;
+  w.len = len;
+  w.span = waste + len;
+  return true;
+}
+
+int ms_server::issue(Wave &w) {
+  if (ev_pool.empty()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess) return MS_ECUDA;
+    if (cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) return MS_ECUDA;
+    ev_pool.push_back({a, b});
+  }
+  w.ev_h2d = ev_pool.back().first;
+  w.ev_done = ev_pool.back().second;
+  ev_pool.pop_back();
+  // slot index of every page of the wave, in order
+  std::vector<std::pair<uint64_t, uint32_t>> map;  // (working-set page, staging slot)
+  map.reserve(w.len);
+  uint32_t k = w.pos;
+  for (uint64_t t : w.tickets) {
+    Req &r = slot(t);
+    r.state.store(kAdmitted, std::memory_order_release);
+    for (uint64_t pg : r.pages) map.push_back({pg, k++});
+  }
+  pool->run(map.size(), [&](size_t i) {
+    const uint64_t pg = map[i].first;
+    const uint32_t sl = map[i].second;
+    std::memcpy(h_stage + (size_t)sl * MS_PAGE_BYTES, host + pg * MS_PAGE_BYTES, MS_PAGE_BYTES);
+    h_ent[sl].addr = (uint64_t)(d_stage + (size_t)sl * MS_PAGE_BYTES);
+    h_ent[sl].page_id = pg;
+  });
+  const size_t off = (size_t)w.pos * MS_PAGE_BYTES, bytes = (size_t)w.len * MS_PAGE_BYTES;
+  cudaStream_t sw = s_work[wave_seq++ & 1];
+  cudaError_t e = cudaMemcpyAsync(d_stage + off, h_stage + off, bytes, cudaMemcpyHostToDevice, s_in);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_ent + w.pos, h_ent + w.pos, sizeof(ms_page) * w.len, cudaMemcpyHostToDevice, s_in);
+  if (e == cudaSuccess) e = cudaEventRecord(w.ev_h2d, s_in);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(sw, w.ev_h2d, 0);
+  if (e == cudaSuccess) {
+    PageArgs a = make_args(ctx);
+    a.pages = d_ent + w.pos;
+    a.n_pages = w.len;
+    e = launch_pages(ctx, a, sw);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_stage + off, d_stage + off, bytes, cudaMemcpyDeviceToHost, sw);
+  if (e == cudaSuccess && cfg.zero_staging) e = cudaMemsetAsync(d_stage + off, 0, bytes, sw);
+  if (e == cudaSuccess) e = cudaEventRecord(w.ev_done, sw);
+  if (e != cudaSuccess) return cuda_fail(ctx, e);
+  ring_head = w.pos + w.len;
+  ring_used += w.span;
+  st_waves.fetch_add(1);
+  atomic_max(st_maxreq, w.tickets.size());
+  atomic_max(st_maxpages, w.len);
+  return MS_OK;
+}
+
+void ms_server::complete(Wave &w) {
+  std::vector<std::pair<uint64_t, uint32_t>> map;
+  map.reserve(w.len);
+  uint32_t k = w.pos;
+  for (uint64_t t : w.tickets)
+    for (uint64_t pg : slot(t).pages) map.push_back({pg, k++});
+  const bool wipe = cfg.zero_staging != 0;
+  pool->run(map.size(), [&](size_t i) {
+    uint8_t *src = h_stage + (size_t)map[i].second * MS_PAGE_BYTES;
+    std::memcpy(host + map[i].first * MS_PAGE_BYTES, src, MS_PAGE_BYTES);
+    if (wipe) std::memset(src, 0, MS_PAGE_BYTES);
+  });
+  const uint64_t t = now_ns();
+  uint64_t pages = 0;
+  {
+    std::lock_guard<std::mutex> lk(qmu);  // busy[] is shared with admission
+    for (uint64_t tk : w.tickets)
+      for (uint64_t pg : slot(tk).pages) busy[pg] = 0;
+  }
+  for (uint64_t tk : w.tickets) {
+    Req &r = slot(tk);
+    pages += r.pages.size();
+    r.t_done_ns.store(t);
+    if (r.lat_out) *r.lat_out = (double)((int64_t)(t - r.t_sched_ns)) * 1e-9;
+    r.state.store(kDone, std::memory_order_release);
+  }
+  ring_used -= w.span;
+  ev_pool.push_back({w.ev_h2d, w.ev_done});
+  st_req.fetch_add(w.tickets.size());
+  st_pages.fetch_add(pages);
+  {
+    std::lock_guard<std::mutex> lk(done_mu);
+  }
+  done_cv.notify_all();
+}
+
+void ms_server::fail_all(int code) {
+  error.store(code);
+  std::lock_guard<std::mutex> lk(qmu);
+  for (Wave &w : inflight)
+    for (uint64_t t : w.tickets) {
+      slot(t).error.store(code);
+      slot(t).state.store(kDone);
+    }
+  for (uint64_t t : incoming) {
+    slot(t).error.store(code);
+    slot(t).state.store(kDone);
+  }
+  incoming.clear();
+  done_cv.notify_all();
+}
+
+void ms_server::loop() {
+  DeviceGuard g(ctx->device);
+  // short naps must stay short: drop this thread's timer slack (default 50 us)
+  prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);
+  uint64_t stop_deadline = 0;
+  uint64_t idle_since = 0;
+  for (;;) {
+    bool progress = false;
+    while (!inflight.empty()) {
+      cudaError_t q = cudaEventQuery(inflight.front().ev_done);
+      if (q == cudaErrorNotReady) break;
+      if (q != cudaSuccess) {
+        cuda_fail(ctx, q);
+        fail_all(MS_ECUDA);
+        exited.store(true);
+        return;
+      }
+      complete(inflight.front());
+      inflight.pop_front();
+      progress = true;
+    }
+    if (stop.load()) {
+      bool empty;
+      {
+        std::lock_guard<std::mutex> lk(qmu);
+        empty = incoming.empty();
+      }
+      if (empty && inflight.empty()) break;
+      if (!stop_deadline) stop_deadline = now_ns() + (uint64_t)ctx->cfg.timeout_ms * 1000000ull;
+      if (now_ns() > stop_deadline) {
+        fail_all(MS_ETIMEDOUT);
+        break;
+      }
+    }
+    if (inflight.size() < cfg.waves_in_flight && error.load() == 0) {
+      Wave w;
+      if (form_wave(w)) {
+        int rc = issue(w);
+        if (rc != MS_OK) {
+          inflight.push_back(w);
+          fail_all(rc);
+          exited.store(true);
+          return;
+        }
+        inflight.push_back(std::move(w));
+        progress = true;
+      }
+    }
+    if (progress) {
+      idle_since = 0;
+      continue;
+    }
+    if (inflight.empty()) {
+      std::unique_lock<std::mutex> lk(qmu);
+      qcv.wait_for(lk, std::chrono::milliseconds(1), [&] { return !incoming.empty() || stop.load(); });
+    } else {
+      // a wave is on the GPU: poll, spinning briefly before napping
+      const uint64_t t = now_ns();
+      if (!idle_since) idle_since = t;
+      if (t - idle_since > 20000) nap_ns(2000);
+    }
+  }
+  exited.store(true);
+}
+
+extern "C" {
+
+void ms_server_config_default(ms_server_config *cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->staging_bytes = (uint64_t)256 << 20;
+  cfg->waves_in_flight = 2;
+  cfg->copy_threads = 4;
+  cfg->max_pending = 1u << 18;
+  cfg->mode = MS_SERVE_CONTINUOUS;
+  cfg->max_request_pages = 4096;
+}
+
+static void free_server(ms_server *s) {
+  if (s->pool) delete s->pool;
+  for (auto &p : s->ev_pool) {
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  if (s->s_in) cudaStreamDestroy(s->s_in);
+  for (auto &w : s->s_work)
+    if (w) cudaStreamDestroy(w);
+  if (s->h_stage) cudaFreeHost(s->h_stage);
+  if (s->h_ent) cudaFreeHost(s->h_ent);
+  if (s->d_stage) cudaFree(s->d_stage);
+  if (s->d_ent) cudaFree(s->d_ent);
+  delete s;
+}
+
+int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_server_config *cfg_in,
+                     ms_server **out) {
+  if (!out) return MS_EINVAL;
+  *out = nullptr;
+  if (!c || !c->alive) return MS_ENOTINIT;
+  if (!host_base || n_pages == 0) return MS_EINVAL;
+  ms_server_config cfg;
+  if (cfg_in) cfg = *cfg_in; else ms_server_config_default(&cfg);
+  if (cfg.staging_bytes == 0) cfg.staging_bytes = (uint64_t)256 << 20;
+  if (cfg.staging_bytes % MS_PAGE_BYTES || cfg.staging_bytes / MS_PAGE_BYTES > (1u << 24)) return MS_EINVAL;
+  if (cfg.waves_in_flight == 0) cfg.waves_in_flight = 2;
+  if (cfg.waves_in_flight > 8 || cfg.copy_threads > 32) return MS_EINVAL;
+  if (cfg.max_pending == 0) cfg.max_pending = 1u << 18;
+  if (cfg.max_pending > (1u << 24)) return MS_EINVAL;
+  if (cfg.mode != MS_SERVE_CONTINUOUS && cfg.mode != MS_SERVE_ONE_PER_LAUNCH) return MS_EINVAL;
+  const uint32_t S = (uint32_t)(cfg.staging_bytes / MS_PAGE_BYTES);
+  if (cfg.max_wave_pages == 0) cfg.max_wave_pages = std::max<uint32_t>(1, S / cfg.waves_in_flight);
+  if (cfg.max_request_pages == 0) cfg.max_request_pages = 4096;
+  if (cfg.max_request_pages > S || cfg.max_request_pages > cfg.max_wave_pages) return MS_EINVAL;
+
+  ms_server *s = new (std::nothrow) ms_server();
+  if (!s) return MS_ENOMEM;
+  s->ctx = c;
+  s->host = (uint8_t *)host_base;
+  s->n_pages = n_pages;
+  s->cfg = cfg;
+  s->S = S;
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaHostAlloc(&s->h_stage, (size_t)S * MS_PAGE_BYTES, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc(&s->h_ent, (size_t)S * sizeof(ms_page), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_stage, (size_t)S * MS_PAGE_BYTES);
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_ent, (size_t)S * sizeof(ms_page));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_work[0], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_work[1], cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    free_server(s);
+    return e == cudaErrorMemoryAllocation ? MS_ENOMEM : cuda_fail(c, e);
+  }
+  try {
+    s->reqs = std::vector<Req>(cfg.max_pending);
+    s->busy.assign(n_pages, 0);
+    s->pool = new CopyPool((int)cfg.copy_threads);
+    s->th = std::thread([s] { s->loop(); });
+  } catch (...) {
+    free_server(s);
+    return MS_ENOMEM;
+  }
+  *out = s;
+  return MS_OK;
+}
+
+static int submit_internal(ms_server *s, int op, const uint64_t *page_index, uint32_t n, uint64_t *ticket,
+                           uint64_t t_sched, double *lat_out) {
+  if (!s) return MS_EINVAL;
+  if (op != MS_ENCRYPT && op != MS_DECRYPT) return MS_EINVAL;
+  if (n == 0 || !page_index) return MS_EINVAL;
+  if (n > s->cfg.max_request_pages) return MS_ERANGE;
+  if (s->error.load()) return s->error.load();
+  if (s->stop.load()) return MS_ENOTINIT;
+  for (uint32_t i = 0; i < n; ++i)
+    if (page_index[i] >= s->n_pages) return MS_EINVAL;
+  // distinct pages within a request (two in-place updates of one page in one wave would race)
+  if (n > 1) {
+    std::vector<uint64_t> tmp(page_index, page_index + n);
+    std::sort(tmp.begin(), tmp.end());
+    if (std::adjacent_find(tmp.begin(), tmp.end()) != tmp.end()) return MS_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(s->qmu);
+  const uint64_t t = s->next_ticket.load();
+  Req &r = s->slot(t);
+  int st = r.state.load();
+  if (st == kQueued || st == kAdmitted || st == kClaiming) return MS_EBUSY;
+  r.state.store(kClaiming);
+  r.ticket.store(t);  // before next_ticket: a poll that sees ticket t valid finds the slot claimed
+  s->next_ticket.store(t + 1);
+  r.op = op;
+  r.pages.assign(page_index, page_index + n);
+  r.error.store(0);
+  r.t_done_ns.store(0);
+  r.t_sched_ns = t_sched ? t_sched : now_ns();
+  r.lat_out = lat_out;
+  r.state.store(kQueued, std::memory_order_release);
+  s->incoming.push_back(t);
+  if (ticket) *ticket = t;
+  s->qcv.notify_one();
+  return MS_OK;
+}
+
+int ms_server_submit(ms_server *s, int op, const uint64_t *page_index, uint32_t n, uint64_t *ticket) {
+  return submit_internal(s, op, page_index, n, ticket, 0, nullptr);
+}
+
+int ms_server_poll(ms_server *s, uint64_t ticket) {
+  if (!s) return MS_EINVAL;
+  if (ticket >= s->next_ticket.load()) return MS_EINVAL;
+  Req &r = s->slot(ticket);
+  const uint64_t owner = r.ticket.load();
+  if (owner != ticket) return owner > ticket && owner != ~0ull ? 1 : 0;  // reused: finished long ago
+  const int st = r.state.load(std::memory_order_acquire);
+  if (st != kDone) return 0;
+  const int err = r.error.load();
+  return err ? err : 1;
+}
+
+int ms_server_wait(ms_server *s, uint64_t ticket, uint32_t timeout_ms) {
+  if (!s) return MS_EINVAL;
+  const auto deadline = clk::now() + std::chrono::milliseconds(timeout_ms);
+  for (;;) {
+    int p = ms_server_poll(s, ticket);
+    if (p < 0) return p;
+    if (p == 1) return MS_OK;
+    std::unique_lock<std::mutex> lk(s->done_mu);
+    if (s->done_cv.wait_until(lk, deadline) == std::cv_status::timeout) {
+      p = ms_server_poll(s, ticket);
+      if (p < 0) return p;
+      return p == 1 ? MS_OK : MS_ETIMEDOUT;
+    }
+  }
+}
+
+int ms_server_replay(ms_server *s, size_t n, const double *arrival_s, const int *ops, const uint64_t *offsets,
+                     const uint64_t *page_index, double *latency_s, double *makespan_s, uint32_t timeout_ms) {
+  if (!s || (n && (!arrival_s || !ops || !offsets || !page_index || !latency_s))) return MS_EINVAL;
+  for (size_t r = 0; r < n; ++r) latency_s[r] = -1.0;
+  // precise pacing: short timer slack for this thread while replaying
+  const int old_slack = prctl(PR_GET_TIMERSLACK, 0, 0, 0, 0);
+  prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);
+  struct SlackRestore {
+    int v;
+    ~SlackRestore() {
+      if (v > 0) prctl(PR_SET_TIMERSLACK, (unsigned long)v, 0, 0, 0);
+    }
+  } restore{old_slack};
+  const uint64_t t0 = now_ns() + 1000000ull;  // start 1 ms from now
+  std::vector<uint64_t> tickets(n);
+  for (size_t r = 0; r < n; ++r) {
+    const uint64_t target = t0 + (uint64_t)(arrival_s[r] * 1e9);
+    for (;;) {
+      const uint64_t t = now_ns();
+      if (t >= target) break;
+      if (target - t > 200000) nap_ns((long)(target - t - 100000));
+    }
+    const uint64_t n_pg = offsets[r + 1] - offsets[r];
+    const uint64_t spin_limit = now_ns() + (uint64_t)timeout_ms * 1000000ull;
+    for (;;) {
+      int rc = submit_internal(s, ops[r], page_index + offsets[r], (uint32_t)n_pg, &tickets[r], target, &latency_s[r]);
+      if (rc == MS_OK) break;
+      if (rc != MS_EBUSY) return rc;
+      if (now_ns() > spin_limit) return MS_ETIMEDOUT;
+      nap_ns(5000);
+    }
+  }
+  const uint64_t deadline = now_ns() + (uint64_t)timeout_ms * 1000000ull;
+  uint64_t last = t0;
+  for (size_t r = 0; r < n; ++r) {
+    for (;;) {
+      int p = ms_server_poll(s, tickets[r]);
+      if (p < 0) return p;
+      if (p == 1) break;
+      if (now_ns() > deadline) return MS_ETIMEDOUT;
+      nap_ns(5000);
+    }
+  }
+  for (size_t r = 0; r < n; ++r) {
+    const uint64_t target = t0 + (uint64_t)(arrival_s[r] * 1e9);
+    last = std::max(last, target + (uint64_t)std::max(0.0, latency_s[r] * 1e9));
+  }
+  if (makespan_s) *makespan_s = (double)(last - t0) * 1e-9;
+  return MS_OK;
+}
+
+int ms_server_get_stats(const ms_server *s, ms_server_stats *out) {
+  if (!s || !out) return MS_EINVAL;
+  out->requests_done = s->st_req.load();
+  out->pages_done = s->st_pages.load();
+  out->waves = s->st_waves.load();
+  out->max_wave_requests = s->st_maxreq.load();
+  out->max_wave_pages = s->st_maxpages.load();
+  out->conflict_waits = s->st_conflict.load();
+  out->budget_waits = s->st_budget.load();
+  return MS_OK;
+}
+
+int ms_server_destroy(ms_server *s) {
+  if (!s) return MS_OK;
+  s->stop.store(true);
+  s->qcv.notify_all();
+  if (s->th.joinable()) s->th.join();
+  int rc = s->error.load();
+  DeviceGuard g(s->ctx->device);
+  // everything the server issued must be finished before its buffers go
+  for (Wave &w : s->inflight) {
+    int r = wait_event(s->ctx, w.ev_done, s->ctx->cfg.timeout_ms);
+    if (r != MS_OK) return r;  // still running on the GPU: leave the buffers allocated
+  }
+  free_server(s);
+  return rc == MS_ETIMEDOUT ? MS_ETIMEDOUT : (rc ? rc : MS_OK);
+}
+
+}  // extern "C"

@@ -85,6 +85,27 @@ class ms_tune_result(ctypes.Structure):
     ]
 
 
+class ms_server_config(ctypes.Structure):
+    _fields_ = [
+        ("staging_bytes", ctypes.c_uint64),
+        ("max_wave_pages", ctypes.c_uint32),
+        ("waves_in_flight", ctypes.c_uint32),
+        ("copy_threads", ctypes.c_uint32),
+        ("max_pending", ctypes.c_uint32),
+        ("mode", ctypes.c_uint32),
+        ("zero_staging", ctypes.c_uint32),
+        ("max_request_pages", ctypes.c_uint32),
+    ]
+
+
+class ms_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("requests_done", "pages_done", "waves", "max_wave_requests",
+                                               "max_wave_pages", "conflict_waits", "budget_waits")]
+
+
+MS_SERVE_CONTINUOUS, MS_SERVE_ONE_PER_LAUNCH = 0, 1
+
+
 def _load():
     path = _build.LIB
     if not os.path.exists(path):
@@ -119,6 +140,14 @@ def _load():
         "ms_batch_get_stats": (I, [P, ctypes.POINTER(ms_batch_stats)]),
         "ms_batch_destroy": (I, [P]),
         "ms_autotune": (I, [P, S, ctypes.POINTER(ms_tune_result)]),
+        "ms_server_config_default": (None, [ctypes.POINTER(ms_server_config)]),
+        "ms_server_create": (I, [P, P, U64, ctypes.POINTER(ms_server_config), ctypes.POINTER(P)]),
+        "ms_server_submit": (I, [P, I, P, ctypes.c_uint32, ctypes.POINTER(U64)]),
+        "ms_server_poll": (I, [P, U64]),
+        "ms_server_wait": (I, [P, U64, ctypes.c_uint32]),
+        "ms_server_replay": (I, [P, S, P, P, P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.c_uint32]),
+        "ms_server_get_stats": (I, [P, ctypes.POINTER(ms_server_stats)]),
+        "ms_server_destroy": (I, [P]),
         "ms_tune_save": (I, [P, ctypes.c_char_p]),
         "ms_tune_load": (I, [P, ctypes.c_char_p]),
     }
@@ -337,6 +366,78 @@ class Batch:
     def destroy(self) -> int:
         if self.handle:
             rc = _lib.ms_batch_destroy(self.handle)
+            self.handle = None
+            return rc
+        return MS_OK
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+
+class Server:
+    """An ms_server: continuous batching of page requests over a host working set."""
+
+    def __init__(self, ctx: Context, host_base, n_pages: int, *, staging_bytes: int = 0, max_wave_pages: int = 0,
+                 waves_in_flight: int = 0, copy_threads: int | None = None, max_pending: int = 0,
+                 mode: int = MS_SERVE_CONTINUOUS, zero_staging: bool = False, max_request_pages: int = 0):
+        cfg = ms_server_config()
+        _lib.ms_server_config_default(ctypes.byref(cfg))
+        if staging_bytes:
+            cfg.staging_bytes = staging_bytes
+        if max_wave_pages:
+            cfg.max_wave_pages = max_wave_pages
+        if waves_in_flight:
+            cfg.waves_in_flight = waves_in_flight
+        if copy_threads is not None:
+            cfg.copy_threads = copy_threads
+        if max_pending:
+            cfg.max_pending = max_pending
+        cfg.mode = mode
+        cfg.zero_staging = 1 if zero_staging else 0
+        if max_request_pages:
+            cfg.max_request_pages = max_request_pages
+        h = ctypes.c_void_p()
+        _check(_lib.ms_server_create(ctx.handle, _ptr(host_base), n_pages, ctypes.byref(cfg), ctypes.byref(h)),
+               "ms_server_create")
+        self.handle = h.value
+        self.ctx = ctx
+
+    def submit(self, op: int, page_index) -> int:
+        idx = np.ascontiguousarray(page_index, dtype=np.uint64)
+        t = ctypes.c_uint64()
+        _check(_lib.ms_server_submit(self.handle, op, idx.ctypes.data, idx.size, ctypes.byref(t)), "ms_server_submit")
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        return _lib.ms_server_poll(self.handle, ticket)
+
+    def wait(self, ticket: int, timeout_ms: int = 10000) -> None:
+        _check(_lib.ms_server_wait(self.handle, ticket, timeout_ms), "ms_server_wait")
+
+    def replay(self, arrival_s, ops, offsets, page_index, timeout_ms: int = 60000):
+        """Open-loop replay; returns (latency_s array, makespan_s)."""
+        arrival_s = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        ops = np.ascontiguousarray(ops, dtype=np.int32)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        page_index = np.ascontiguousarray(page_index, dtype=np.uint64)
+        lat = np.empty(arrival_s.size, dtype=np.float64)
+        mk = ctypes.c_double()
+        _check(_lib.ms_server_replay(self.handle, arrival_s.size, arrival_s.ctypes.data, ops.ctypes.data,
+                                     offsets.ctypes.data, page_index.ctypes.data, lat.ctypes.data,
+                                     ctypes.byref(mk), timeout_ms), "ms_server_replay")
+        return lat, mk.value
+
+    def stats(self) -> dict:
+        st = ms_server_stats()
+        _check(_lib.ms_server_get_stats(self.handle, ctypes.byref(st)), "ms_server_get_stats")
+        return {f: getattr(st, f) for f, _ in ms_server_stats._fields_}
+
+    def destroy(self) -> int:
+        if self.handle:
+            rc = _lib.ms_server_destroy(self.handle)
             self.handle = None
             return rc
         return MS_OK

@@ -1,0 +1,147 @@
+"""GPU tests of the served form (continuous batching over a pinned host
+working set): results match the oracle, each request's result is the same
+alone and in the mix, admission respects page conflicts and the budget."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import PAGE
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ms():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2004_09252_b300 import memshield
+    return memshield
+
+
+def working_set(seed, n):
+    h = torch.empty(n * PAGE, dtype=torch.uint8).pin_memory()
+    synth.fill_pages(h.data_ptr(), seed, 0, n)
+    return h
+
+
+def distinct_workload(seed, n_req, n_pages, rate):
+    """Serving recipe (80 % 1-page decrypts, 20 % 8..64-page encrypts, Poisson
+    arrivals) with every page used by at most one request, so each request's
+    output is just its pages' final contents."""
+    arrival, ops, offsets, _ = synth.serving_workload(seed, n_req, rate, n_pages)
+    total = int(offsets[-1])
+    pages = synth.scattered_slots(seed + 7, n_pages, total)
+    return arrival, ops, offsets, pages
+
+
+def oracle_ws(key, plain, pages):
+    want = plain.copy()
+    oracle.crypt_pages(key, want, pages, pages, threads=8)
+    return want
+
+
+def test_submit_wait_matches_oracle(ms, key1):
+    n = 2048
+    h = working_set(70, n)
+    plain = h.numpy().copy()
+    reqs = [(1, [5]), (0, list(range(100, 140))), (1, [2047]), (0, [7, 9, 11, 1000, 3])]
+    with ms.Context(key1) as ctx, ms.Server(ctx, h, n) as srv:
+        tickets = [srv.submit(op, pg) for op, pg in reqs]
+        for t in tickets:
+            srv.wait(t)
+            assert srv.poll(t) == 1
+        st = srv.stats()
+    touched = np.array(sorted({p for _, pg in reqs for p in pg}), dtype=np.uint64)
+    assert np.array_equal(h.numpy(), oracle_ws(key1, plain, touched))
+    assert st["requests_done"] == len(reqs) and st["pages_done"] == len(touched)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_alone_equals_mix(ms, key1, mode):
+    """Each request's result is identical when served alone (submit, wait, one
+    at a time) and when served in a fast open-loop mix (bit-exact), and both
+    equal the oracle."""
+    n, n_req = 16384, 1500
+    arrival, ops, offsets, pages = distinct_workload(71, n_req, n, 2e6)
+    plain = synth.page_bytes_fast(72, 0, n)
+    alone = torch.from_numpy(plain.copy()).pin_memory()
+    mix = torch.from_numpy(plain.copy()).pin_memory()
+    with ms.Context(key1) as ctx:
+        with ms.Server(ctx, alone, n) as srv:
+            for r in range(n_req):
+                srv.wait(srv.submit(int(ops[r]), pages[offsets[r]:offsets[r + 1]]))
+        with ms.Server(ctx, mix, n, mode=mode) as srv:
+            lat, makespan = srv.replay(arrival, ops, offsets, pages)
+            st = srv.stats()
+    assert (lat >= 0).all() and makespan > 0
+    a, b = alone.numpy().reshape(n, PAGE), mix.numpy().reshape(n, PAGE)
+    for r in range(n_req):
+        sel = pages[offsets[r]:offsets[r + 1]]
+        assert np.array_equal(a[sel], b[sel]), f"request {r} differs alone vs mix"
+    assert np.array_equal(alone.numpy(), oracle_ws(key1, plain, pages))
+    if mode == 1:
+        assert st["max_wave_requests"] == 1 and st["waves"] == n_req
+    else:
+        assert st["waves"] <= n_req
+
+
+def test_conflicting_requests_serialise(ms, key1):
+    """Requests on the same pages wait for each other; k applications of the
+    same XOR leave p ^ K for odd k and p for even k."""
+    n = 256
+    h = working_set(73, n)
+    plain = h.numpy().copy()
+    rng = synth.splitmix64(74, 0, 4000)
+    counts = np.zeros(n, dtype=np.int64)
+    with ms.Context(key1) as ctx, ms.Server(ctx, h, n, max_request_pages=16) as srv:
+        tickets = []
+        for r in range(200):
+            k = 1 + int(rng[r] % np.uint64(16))
+            sel = np.unique((rng[200 + 16 * r:200 + 16 * r + k] % np.uint64(32)).astype(np.int64))
+            counts[sel] += 1
+            tickets.append(srv.submit(r % 2, sel))
+        for t in tickets:
+            srv.wait(t)
+        st = srv.stats()
+    odd = np.nonzero(counts % 2)[0].astype(np.uint64)
+    assert np.array_equal(h.numpy(), oracle_ws(key1, plain, odd))
+    assert st["conflict_waits"] > 0
+
+
+def test_small_staging_budget(ms, key1):
+    n, n_req = 4096, 400
+    arrival, ops, offsets, pages = distinct_workload(75, n_req, n, 5e5)
+    sizes = np.diff(offsets)
+    keep = sizes <= 32
+    # requests of at most 32 pages through a 64-page staging ring
+    sel_req = np.nonzero(keep)[0]
+    new_off = np.concatenate([[0], np.cumsum(sizes[sel_req])]).astype(np.uint64)
+    new_pages = np.concatenate([pages[offsets[r]:offsets[r + 1]] for r in sel_req])
+    plain = synth.page_bytes_fast(76, 0, n)
+    h = torch.from_numpy(plain.copy()).pin_memory()
+    with ms.Context(key1) as ctx, ms.Server(ctx, h, n, staging_bytes=64 * PAGE, max_request_pages=32,
+                                            zero_staging=True) as srv:
+        lat, _ = srv.replay(arrival[sel_req], ops[sel_req], new_off, new_pages)
+        st = srv.stats()
+    assert np.array_equal(h.numpy(), oracle_ws(key1, plain, new_pages))
+    assert st["max_wave_pages"] <= 32 and st["budget_waits"] > 0
+
+
+def test_limits(ms, key1):
+    n = 64
+    h = working_set(77, n)
+    plain = h.numpy().copy()
+    with ms.Context(key1) as ctx, ms.Server(ctx, h, n, max_request_pages=8) as srv:
+        for bad, code in (([1] * 2, ms.MS_EINVAL), ([64], ms.MS_EINVAL), (list(range(9)), ms.MS_ERANGE)):
+            with pytest.raises(ms.MemShieldError) as e:
+                srv.submit(ms.MS_ENCRYPT, bad)
+            assert e.value.code == code
+        with pytest.raises(ms.MemShieldError):
+            srv.submit(3, [1])
+        assert srv.poll(10**9) == ms.MS_EINVAL
+    assert np.array_equal(h.numpy(), plain)
+    with ms.Context(key1) as ctx:
+        with pytest.raises(ms.MemShieldError):
+            ms.Server(ctx, h, n, staging_bytes=1000)      # not a multiple of 4096
