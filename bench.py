@@ -534,6 +534,68 @@ def run_host(args):
     }), flush=True)
 
 
+# ------------------------------------------------------- serving (config 5)
+SERVE_RATES = [1e4, 3.76e4, 1.41e5, 5.32e5, 2e6]
+
+
+def run_serving(args):
+    """Poisson arrivals at 5 page rates; 80 % 1-page decrypts, 20 % 8..64-page
+    encrypts over a 16 GiB pinned host working set (seed 5); 256 MiB staging
+    budget; continuous batching vs one launch per request."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2004_09252_b300 import memshield as ms
+
+    n = args.serve_pages
+    key = synth.key_bytes(1)
+    t0 = time.perf_counter()
+    ws = torch.empty(n * PAGE, dtype=torch.uint8).pin_memory()
+    synth.fill_pages(ws.data_ptr(), 5, 0, n)
+    setup_s = time.perf_counter() - t0
+    ctx = ms.Context(key)
+    ctx.autotune(65536)
+    rows = []
+    for rate in args.serve_rates:
+        n_req = max(2000, int(rate / 8.0 * args.serve_seconds))
+        arrival, ops, offsets, pages = synth.serving_workload(5, n_req, rate, n)
+        for mode, name in ((ms.MS_SERVE_CONTINUOUS, "continuous"), (ms.MS_SERVE_ONE_PER_LAUNCH, "one_per_launch")):
+            with ms.Server(ctx, ws, n, mode=mode, copy_threads=args.copy_threads) as srv:
+                lat, makespan = srv.replay(arrival, ops, offsets, pages, timeout_ms=600000)
+                st = srv.stats()
+            total = int(offsets[-1])
+            us = lat * 1e6
+            rows.append({"offered_pages_per_s": rate, "mode": name, "requests": n_req, "pages": total,
+                         "sustained_pages_per_s": round(total / makespan, 1),
+                         "p50_us": round(float(np.percentile(us, 50)), 1),
+                         "p99_us": round(float(np.percentile(us, 99)), 1),
+                         "p999_us": round(float(np.percentile(us, 99.9)), 1),
+                         "waves": st["waves"], "max_wave_requests": st["max_wave_requests"],
+                         "conflict_waits": st["conflict_waits"], "budget_waits": st["budget_waits"]})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    ctx.shutdown()
+    cont = [r for r in rows if r["mode"] == "continuous"]
+    one = {r["offered_pages_per_s"]: r for r in rows if r["mode"] == "one_per_launch"}
+    top = cont[-1]
+    print(json.dumps({
+        "metric": "served pages/s and p50/p99 request latency (continuous batching)",
+        "value": top["sustained_pages_per_s"], "unit": "pages/s", "higher_is_better": True,
+        "config": {"workload": f"serving: {n} pages ({n * PAGE / 2**30:.0f} GiB) pinned host working set (seed 5), "
+                               "Poisson arrivals, 80 % 1-page decrypts / 20 % U{8..64}-page encrypts, 256 MiB "
+                               f"staging budget, {args.serve_seconds:g} s per rate",
+                   "rates_pages_per_s": args.serve_rates, "copy_threads": args.copy_threads,
+                   "working_set_setup_s": round(setup_s, 1)},
+        "p50_us": top["p50_us"], "p99_us": top["p99_us"], "p999_us": top["p999_us"],
+        "vs_one_per_launch": [{"offered": r["offered_pages_per_s"],
+                               "sustained_ratio": round(r["sustained_pages_per_s"] /
+                                                        one[r["offered_pages_per_s"]]["sustained_pages_per_s"], 3),
+                               "p99_ratio": round(one[r["offered_pages_per_s"]]["p99_us"] / r["p99_us"], 3)}
+                              for r in cont],
+        "rows": rows,
+    }), flush=True)
+
+
 # -------------------------------------------------------------- reference
 def run_reference(args):
     rank, world, _ = env_rank()
@@ -594,8 +656,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-chunk-mib", type=int, default=16)
     ap.add_argument("--e2e-streams", type=int, default=2)
-    ap.add_argument("--workload", choices=["bulk", "batching", "host"], default="bulk",
-                    help="bulk (default, the contract line); batching / host print their own line")
+    ap.add_argument("--workload", choices=["bulk", "batching", "host", "serving"], default="bulk",
+                    help="bulk (default, the contract line); batching / host / serving print their own line")
+    ap.add_argument("--serve-pages", type=int, default=4194304, help="working-set pages (default 16 GiB)")
+    ap.add_argument("--serve-rates", type=lambda v: [float(x) for x in v.split(",")], default=SERVE_RATES)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--copy-threads", type=int, default=4)
     ap.add_argument("--batch-requests", type=lambda v: [int(x) for x in v.split(",")],
                     default=[1, 16, 256, 2000, 20000])
     ap.add_argument("--chunks-mib", type=lambda v: [int(x) for x in v.split(",")], default=[2, 4, 8, 16, 32, 64])
@@ -608,6 +674,8 @@ def main():
         run_batching(args)
     elif args.workload == "host":
         run_host(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 
