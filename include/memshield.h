@@ -310,6 +310,7 @@ typedef struct ms_server_stats {
   uint64_t max_wave_pages;
   uint64_t conflict_waits;   /* times the head request waited for an in-flight page */
   uint64_t budget_waits;     /* times the head request waited for staging room */
+  uint64_t max_staged_pages; /* most staging slots ever in use (never above the budget) */
 } ms_server_stats;
 
 void ms_server_config_default(ms_server_config *cfg);

@@ -165,7 +165,7 @@ struct ms_server {
   std::mutex done_mu;
   std::condition_variable done_cv;
   std::atomic<uint64_t> st_req{0}, st_pages{0}, st_waves{0}, st_maxreq{0}, st_maxpages{0}, st_conflict{0},
-      st_budget{0};
+      st_budget{0}, st_maxstaged{0};
 
   Req &slot(uint64_t t) { return reqs[t % reqs.size()]; }
   void loop();
@@ -276,6 +276,7 @@ int ms_server::issue(Wave &w) {
   if (e != cudaSuccess) return cuda_fail(ctx, e);
   ring_head = w.pos + w.len;
   ring_used += w.span;
+  atomic_max(st_maxstaged, ring_used);
   st_waves.fetch_add(1);
   atomic_max(st_maxreq, w.tickets.size());
   atomic_max(st_maxpages, w.len);
@@ -609,6 +610,7 @@ int ms_server_get_stats(const ms_server *s, ms_server_stats *out) {
   out->max_wave_pages = s->st_maxpages.load();
   out->conflict_waits = s->st_conflict.load();
   out->budget_waits = s->st_budget.load();
+  out->max_staged_pages = s->st_maxstaged.load();
   return MS_OK;
 }
 
