@@ -340,6 +340,12 @@ def run_ours(args):
         "clocks": sampler.summary(),
         "e2e": e2e,
     }
+    if not args.no_serving and world == 1:
+        rows, _ = serve_rows(args, [1.41e5, 2e6], ["continuous", "one_per_launch"], 2.0)
+        line["serving"] = {
+            "workload": SERVE_WORKLOAD.format(n=args.serve_pages, gib=args.serve_pages * PAGE / 2**30, sec=2.0),
+            "rows": [{k: r[k] for k in ("offered_pages_per_s", "mode", "sustained_pages_per_s", "p50_us", "p99_us",
+                                        "p999_us")} for r in rows]}
     if rank == 0 and world == 1 and not args.no_cpu:
         threads = host_cores()
         v, npg, dt, passes = cpu_oracle_rate(args.cpu_seconds, threads)
@@ -542,6 +548,35 @@ def run_serving(args):
     """Poisson arrivals at 5 page rates; 80 % 1-page decrypts, 20 % 8..64-page
     encrypts over a 16 GiB pinned host working set (seed 5); 256 MiB staging
     budget; continuous batching vs one launch per request."""
+    rows, setup_s = serve_rows(args, args.serve_rates, args.serve_modes, args.serve_seconds)
+    n = args.serve_pages
+    cont = [r for r in rows if r["mode"] == "continuous"]
+    one = {r["offered_pages_per_s"]: r for r in rows if r["mode"] == "one_per_launch"}
+    if not one:
+        one = {r["offered_pages_per_s"]: r for r in cont}
+    top = cont[-1]
+    print(json.dumps({
+        "metric": "served pages/s and p50/p99 request latency (continuous batching)",
+        "value": top["sustained_pages_per_s"], "unit": "pages/s", "higher_is_better": True,
+        "config": {"workload": SERVE_WORKLOAD.format(n=n, gib=n * PAGE / 2**30, sec=args.serve_seconds),
+                   "rates_pages_per_s": args.serve_rates, "copy_threads": args.copy_threads,
+                   "working_set_setup_s": round(setup_s, 1)},
+        "p50_us": top["p50_us"], "p99_us": top["p99_us"], "p999_us": top["p999_us"],
+        "vs_one_per_launch": [{"offered": r["offered_pages_per_s"],
+                               "sustained_ratio": round(r["sustained_pages_per_s"] /
+                                                        one[r["offered_pages_per_s"]]["sustained_pages_per_s"], 3),
+                               "p99_ratio": round(one[r["offered_pages_per_s"]]["p99_us"] / r["p99_us"], 3)}
+                              for r in cont],
+        "rows": rows,
+    }), flush=True)
+
+
+SERVE_WORKLOAD = ("serving: {n} pages ({gib:.0f} GiB) pinned host working set (seed 5), Poisson arrivals, 80 % "
+                  "1-page decrypts / 20 % U{{8..64}}-page encrypts, 256 MiB staging budget, {sec:g} s per rate")
+
+
+def serve_rows(args, rates, modes, seconds):
+    """Replay the serving workload at each rate in each mode; one row per (rate, mode)."""
     import numpy as np
     import torch
 
@@ -557,10 +592,13 @@ def run_serving(args):
     ctx = ms.Context(key)
     ctx.autotune(65536)
     rows = []
-    for rate in args.serve_rates:
-        n_req = max(2000, int(rate / 8.0 * args.serve_seconds))
+    for rate in rates:
+        n_req = max(2000, int(rate / 8.0 * seconds))
         arrival, ops, offsets, pages = synth.serving_workload(5, n_req, rate, n)
-        for mode, name in ((ms.MS_SERVE_CONTINUOUS, "continuous"), (ms.MS_SERVE_ONE_PER_LAUNCH, "one_per_launch")):
+        modes = {"continuous": ms.MS_SERVE_CONTINUOUS, "one_per_launch": ms.MS_SERVE_ONE_PER_LAUNCH,
+                 "zero_copy": ms.MS_SERVE_ZERO_COPY}
+        for name in modes:
+            mode = modes[name]
             with ms.Server(ctx, ws, n, mode=mode, copy_threads=args.copy_threads) as srv:
                 lat, makespan = srv.replay(arrival, ops, offsets, pages, timeout_ms=600000)
                 st = srv.stats()
@@ -572,28 +610,12 @@ def run_serving(args):
                          "p99_us": round(float(np.percentile(us, 99)), 1),
                          "p999_us": round(float(np.percentile(us, 99.9)), 1),
                          "waves": st["waves"], "max_wave_requests": st["max_wave_requests"],
-                         "conflict_waits": st["conflict_waits"], "budget_waits": st["budget_waits"]})
+                         "conflict_waits": st["conflict_waits"], "budget_waits": st["budget_waits"],
+                         "gather_s": round(st["gather_ns"] * 1e-9, 3), "scatter_s": round(st["scatter_ns"] * 1e-9, 3)})
             print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     ctx.shutdown()
-    cont = [r for r in rows if r["mode"] == "continuous"]
-    one = {r["offered_pages_per_s"]: r for r in rows if r["mode"] == "one_per_launch"}
-    top = cont[-1]
-    print(json.dumps({
-        "metric": "served pages/s and p50/p99 request latency (continuous batching)",
-        "value": top["sustained_pages_per_s"], "unit": "pages/s", "higher_is_better": True,
-        "config": {"workload": f"serving: {n} pages ({n * PAGE / 2**30:.0f} GiB) pinned host working set (seed 5), "
-                               "Poisson arrivals, 80 % 1-page decrypts / 20 % U{8..64}-page encrypts, 256 MiB "
-                               f"staging budget, {args.serve_seconds:g} s per rate",
-                   "rates_pages_per_s": args.serve_rates, "copy_threads": args.copy_threads,
-                   "working_set_setup_s": round(setup_s, 1)},
-        "p50_us": top["p50_us"], "p99_us": top["p99_us"], "p999_us": top["p999_us"],
-        "vs_one_per_launch": [{"offered": r["offered_pages_per_s"],
-                               "sustained_ratio": round(r["sustained_pages_per_s"] /
-                                                        one[r["offered_pages_per_s"]]["sustained_pages_per_s"], 3),
-                               "p99_ratio": round(one[r["offered_pages_per_s"]]["p99_us"] / r["p99_us"], 3)}
-                              for r in cont],
-        "rows": rows,
-    }), flush=True)
+    del ws
+    return rows, setup_s
 
 
 # -------------------------------------------------------------- reference
@@ -653,6 +675,7 @@ def main():
     ap.add_argument("--shape", default="", help="K1 shape override: bpt,tpc,unroll,rot_policy")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the short serving summary in the bulk line")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-chunk-mib", type=int, default=16)
     ap.add_argument("--e2e-streams", type=int, default=2)
@@ -661,7 +684,8 @@ def main():
     ap.add_argument("--serve-pages", type=int, default=4194304, help="working-set pages (default 16 GiB)")
     ap.add_argument("--serve-rates", type=lambda v: [float(x) for x in v.split(",")], default=SERVE_RATES)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
-    ap.add_argument("--copy-threads", type=int, default=4)
+    ap.add_argument("--copy-threads", type=int, default=8)
+    ap.add_argument("--serve-modes", type=lambda v: v.split(","), default=["continuous", "one_per_launch"])
     ap.add_argument("--batch-requests", type=lambda v: [int(x) for x in v.split(",")],
                     default=[1, 16, 256, 2000, 20000])
     ap.add_argument("--chunks-mib", type=lambda v: [int(x) for x in v.split(",")], default=[2, 4, 8, 16, 32, 64])

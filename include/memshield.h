@@ -267,8 +267,9 @@ int ms_tune_load(ms_ctx *ctx, const char *path);
  * encrypted, and both are served from a working set in host RAM.  A server
  * thread admits requests in arrival order while the pinned staging budget
  * has room and none of the request's pages is already in flight (a request
- * touching an in-flight page waits for it, so results do not depend on the
- * mix).  Admitted requests form a wave:
+ * touching an in-flight page waits for it, and so does any later request
+ * sharing a page with a waiting one, so results do not depend on the mix;
+ * requests on other pages go ahead).  Admitted requests form a wave:
  *   - worker threads copy its pages from the working set into pinned
  *     staging (the paper's data thread copying into the shared page);
  *   - the pages go host->device on one stream, through the page kernel and
@@ -289,7 +290,11 @@ int ms_tune_load(ms_ctx *ctx, const char *path);
  */
 typedef struct ms_server ms_server;
 
-enum ms_serve_mode { MS_SERVE_CONTINUOUS = 0, MS_SERVE_ONE_PER_LAUNCH = 1 };
+/* MS_SERVE_ZERO_COPY: no staging copies; the kernel reads and writes the
+ * working set directly over the host link (it must be pinned, mapped memory,
+ * e.g. from cudaHostAlloc); the staging budget then only bounds the pages in
+ * flight.  Requests are admitted the same way. */
+enum ms_serve_mode { MS_SERVE_CONTINUOUS = 0, MS_SERVE_ONE_PER_LAUNCH = 1, MS_SERVE_ZERO_COPY = 2 };
 
 typedef struct ms_server_config {
   uint64_t staging_bytes;    /* admission budget in pinned staging (default 256 MiB, multiple of 4096) */
@@ -300,6 +305,7 @@ typedef struct ms_server_config {
   uint32_t mode;             /* ms_serve_mode */
   uint32_t zero_staging;     /* nonzero: wipe staging pages after each wave */
   uint32_t max_request_pages;/* largest request accepted (default 4096; <= staging pages) */
+  uint32_t idle_spin_us;     /* idle server thread polls this long before sleeping (default 200) */
 } ms_server_config;
 
 typedef struct ms_server_stats {
@@ -311,6 +317,8 @@ typedef struct ms_server_stats {
   uint64_t conflict_waits;   /* times the head request waited for an in-flight page */
   uint64_t budget_waits;     /* times the head request waited for staging room */
   uint64_t max_staged_pages; /* most staging slots ever in use (never above the budget) */
+  uint64_t gather_ns;        /* server-thread time spent copying pages into staging */
+  uint64_t scatter_ns;       /* ... and back into the working set */
 } ms_server_stats;
 
 void ms_server_config_default(ms_server_config *cfg);

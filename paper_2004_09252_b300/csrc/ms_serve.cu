@@ -65,13 +65,14 @@ class CopyPool {
     {
       std::lock_guard<std::mutex> lk(mu_);
       stop_ = true;
+      stop_flag_.store(true);
     }
     cv_.notify_all();
     for (auto &t : th_) t.join();
   }
   // Runs fn(i) for i in [0, n); the calling thread takes part.
   void run(size_t n, const std::function<void(size_t)> &fn) {
-    if (th_.empty() || n < 64) {
+    if (th_.empty() || n < 128) {  // below ~512 KiB one thread is faster than a hand-off
       for (size_t i = 0; i < n; ++i) fn(i);
       return;
     }
@@ -82,6 +83,7 @@ class CopyPool {
       next_.store(0);
       active_ = (int)th_.size();
       ++gen_;
+      pub_gen_.store(gen_, std::memory_order_release);
     }
     cv_.notify_all();
     drain(fn, n);
@@ -100,10 +102,14 @@ class CopyPool {
     }
   }
   void worker() {
+    prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);
     uint64_t seen = 0;
     for (;;) {
       const std::function<void(size_t)> *job;
       size_t n;
+      // poll for a new job for ~100 us before sleeping: waves come in bursts
+      for (int i = 0; i < 100 && pub_gen_.load(std::memory_order_acquire) == seen && !stop_flag_.load(); ++i)
+        nap_ns(1000);
       {
         std::unique_lock<std::mutex> lk(mu_);
         cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
@@ -127,6 +133,8 @@ class CopyPool {
   std::atomic<size_t> next_{0};
   int active_ = 0;
   uint64_t gen_ = 0;
+  std::atomic<uint64_t> pub_gen_{0};
+  std::atomic<bool> stop_flag_{false};
   bool stop_ = false;
 };
 
@@ -165,7 +173,9 @@ struct ms_server {
   std::mutex done_mu;
   std::condition_variable done_cv;
   std::atomic<uint64_t> st_req{0}, st_pages{0}, st_waves{0}, st_maxreq{0}, st_maxpages{0}, st_conflict{0},
-      st_budget{0}, st_maxstaged{0};
+      st_budget{0}, st_maxstaged{0}, st_gather_ns{0}, st_scatter_ns{0};
+  uint64_t d_host = 0;  // device address of host_base (zero-copy mode)
+  uint64_t idle_spin_ns = 0;
 
   Req &slot(uint64_t t) { return reqs[t % reqs.size()]; }
   void loop();
@@ -185,17 +195,30 @@ void atomic_max(std::atomic<uint64_t> &a, uint64_t v) {
 
 }  // namespace
 
-// Admission: take queued requests in arrival order while they fit.
+// Admission.  Queued requests are scanned in arrival order (at most
+// kScanWindow of them per wave) and admitted while the wave and the staging
+// ring have room.  A request with a page already in flight (or in this wave)
+// is skipped, and its pages are blocked for the rest of the scan, so a later
+// request sharing one of them cannot overtake it; requests on other pages
+// still join.  Running out of staging room ends the scan (no overtaking for
+// room, so large requests are not starved).
+constexpr size_t kScanWindow = 4096;
+
 bool ms_server::form_wave(Wave &w) {
   std::lock_guard<std::mutex> lk(qmu);
   if (ring_used == 0) ring_head = 0;  // nothing in flight: the whole ring is free from slot 0
   uint32_t pos = ring_head, waste = 0, len = 0;
-  size_t taken = 0;
-  for (uint64_t t : incoming) {
-    Req &r = slot(t);
+  const size_t window = std::min(incoming.size(), kScanWindow);
+  std::vector<uint8_t> taken(window, 0);
+  std::vector<uint64_t> blocked;
+  size_t n_taken = 0;
+  for (size_t i = 0; i < window; ++i) {
+    Req &r = slot(incoming[i]);
     const uint32_t n = (uint32_t)r.pages.size();
-    if (cfg.mode == MS_SERVE_ONE_PER_LAUNCH && taken == 1) break;
-    if (len + n > cfg.max_wave_pages && taken > 0) break;
+    if (cfg.mode == MS_SERVE_ONE_PER_LAUNCH && n_taken == 1) break;
+    if (len + n > cfg.max_wave_pages) {
+      if (n_taken > 0) break;
+    }
     // contiguous room in the ring: wrap to slot 0 if the tail is too short
     uint32_t p = pos, wst = waste;
     if (len == 0 && p + n > S) {
@@ -214,17 +237,30 @@ bool ms_server::form_wave(Wave &w) {
       }
     if (conflict) {
       st_conflict.fetch_add(1);
-      break;
+      for (uint64_t pg : r.pages)
+        if (!busy[pg]) {
+          busy[pg] = 2;  // blocked for the rest of this scan
+          blocked.push_back(pg);
+        }
+      continue;
     }
     for (uint64_t pg : r.pages) busy[pg] = 1;
     pos = p;
     waste = wst;
     len += n;
-    w.tickets.push_back(t);
-    ++taken;
+    w.tickets.push_back(incoming[i]);
+    taken[i] = 1;
+    ++n_taken;
   }
-  if (taken == 0) return false;
-  incoming.erase(incoming.begin(), incoming.begin() + (long)taken);
+  for (uint64_t pg : blocked) busy[pg] = 0;
+  if (n_taken == 0) return false;
+  // drop the admitted tickets from the scanned prefix, keeping the others in order
+  std::vector<uint64_t> keep;
+  keep.reserve(window - n_taken);
+  for (size_t i = 0; i < window; ++i)
+    if (!taken[i]) keep.push_back(incoming[i]);
+  incoming.erase(incoming.begin(), incoming.begin() + (long)window);
+  for (size_t i = keep.size(); i-- > 0;) incoming.push_front(keep[i]);
   w.pos = pos;
   w.len = len;
   w.span = waste + len;
@@ -250,16 +286,27 @@ int ms_server::issue(Wave &w) {
     r.state.store(kAdmitted, std::memory_order_release);
     for (uint64_t pg : r.pages) map.push_back({pg, k++});
   }
-  pool->run(map.size(), [&](size_t i) {
-    const uint64_t pg = map[i].first;
-    const uint32_t sl = map[i].second;
-    std::memcpy(h_stage + (size_t)sl * MS_PAGE_BYTES, host + pg * MS_PAGE_BYTES, MS_PAGE_BYTES);
-    h_ent[sl].addr = (uint64_t)(d_stage + (size_t)sl * MS_PAGE_BYTES);
-    h_ent[sl].page_id = pg;
-  });
+  const bool zc = cfg.mode == MS_SERVE_ZERO_COPY;
+  const uint64_t tg = now_ns();
+  if (zc) {  // the kernel works on the working set itself, through the host link
+    for (const auto &m : map) {
+      h_ent[m.second].addr = d_host + m.first * MS_PAGE_BYTES;
+      h_ent[m.second].page_id = m.first;
+    }
+  } else {
+    pool->run(map.size(), [&](size_t i) {
+      const uint64_t pg = map[i].first;
+      const uint32_t sl = map[i].second;
+      std::memcpy(h_stage + (size_t)sl * MS_PAGE_BYTES, host + pg * MS_PAGE_BYTES, MS_PAGE_BYTES);
+      h_ent[sl].addr = (uint64_t)(d_stage + (size_t)sl * MS_PAGE_BYTES);
+      h_ent[sl].page_id = pg;
+    });
+  }
+  st_gather_ns.fetch_add(now_ns() - tg);
   const size_t off = (size_t)w.pos * MS_PAGE_BYTES, bytes = (size_t)w.len * MS_PAGE_BYTES;
   cudaStream_t sw = s_work[wave_seq++ & 1];
-  cudaError_t e = cudaMemcpyAsync(d_stage + off, h_stage + off, bytes, cudaMemcpyHostToDevice, s_in);
+  cudaError_t e = cudaSuccess;
+  if (!zc) e = cudaMemcpyAsync(d_stage + off, h_stage + off, bytes, cudaMemcpyHostToDevice, s_in);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_ent + w.pos, h_ent + w.pos, sizeof(ms_page) * w.len, cudaMemcpyHostToDevice, s_in);
   if (e == cudaSuccess) e = cudaEventRecord(w.ev_h2d, s_in);
@@ -270,8 +317,8 @@ int ms_server::issue(Wave &w) {
     a.n_pages = w.len;
     e = launch_pages(ctx, a, sw);
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h_stage + off, d_stage + off, bytes, cudaMemcpyDeviceToHost, sw);
-  if (e == cudaSuccess && cfg.zero_staging) e = cudaMemsetAsync(d_stage + off, 0, bytes, sw);
+  if (e == cudaSuccess && !zc) e = cudaMemcpyAsync(h_stage + off, d_stage + off, bytes, cudaMemcpyDeviceToHost, sw);
+  if (e == cudaSuccess && cfg.zero_staging && !zc) e = cudaMemsetAsync(d_stage + off, 0, bytes, sw);
   if (e == cudaSuccess) e = cudaEventRecord(w.ev_done, sw);
   if (e != cudaSuccess) return cuda_fail(ctx, e);
   ring_head = w.pos + w.len;
@@ -290,12 +337,16 @@ void ms_server::complete(Wave &w) {
   for (uint64_t t : w.tickets)
     for (uint64_t pg : slot(t).pages) map.push_back({pg, k++});
   const bool wipe = cfg.zero_staging != 0;
-  pool->run(map.size(), [&](size_t i) {
-    uint8_t *src = h_stage + (size_t)map[i].second * MS_PAGE_BYTES;
-    std::memcpy(host + map[i].first * MS_PAGE_BYTES, src, MS_PAGE_BYTES);
-    if (wipe) std::memset(src, 0, MS_PAGE_BYTES);
-  });
+  const uint64_t ts = now_ns();
+  if (cfg.mode != MS_SERVE_ZERO_COPY) {
+    pool->run(map.size(), [&](size_t i) {
+      uint8_t *src = h_stage + (size_t)map[i].second * MS_PAGE_BYTES;
+      std::memcpy(host + map[i].first * MS_PAGE_BYTES, src, MS_PAGE_BYTES);
+      if (wipe) std::memset(src, 0, MS_PAGE_BYTES);
+    });
+  }
   const uint64_t t = now_ns();
+  st_scatter_ns.fetch_add(t - ts);
   uint64_t pages = 0;
   {
     std::lock_guard<std::mutex> lk(qmu);  // busy[] is shared with admission
@@ -388,8 +439,14 @@ void ms_server::loop() {
       continue;
     }
     if (inflight.empty()) {
-      std::unique_lock<std::mutex> lk(qmu);
-      qcv.wait_for(lk, std::chrono::milliseconds(1), [&] { return !incoming.empty() || stop.load(); });
+      // idle: watch the ticket counter for a while before blocking, so a
+      // request that arrives soon is picked up without a wake-up delay
+      const uint64_t seen = next_ticket.load(), t_idle = now_ns();
+      while (next_ticket.load() == seen && !stop.load() && now_ns() - t_idle < idle_spin_ns) nap_ns(1000);
+      if (next_ticket.load() == seen && !stop.load()) {
+        std::unique_lock<std::mutex> lk(qmu);
+        qcv.wait_for(lk, std::chrono::milliseconds(1), [&] { return !incoming.empty() || stop.load(); });
+      }
     } else {
       // a wave is on the GPU: poll, spinning briefly before napping
       const uint64_t t = now_ns();
@@ -411,6 +468,7 @@ void ms_server_config_default(ms_server_config *cfg) {
   cfg->max_pending = 1u << 18;
   cfg->mode = MS_SERVE_CONTINUOUS;
   cfg->max_request_pages = 4096;
+  cfg->idle_spin_us = 200;
 }
 
 static void free_server(ms_server *s) {
@@ -443,7 +501,8 @@ int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_serv
   if (cfg.waves_in_flight > 8 || cfg.copy_threads > 32) return MS_EINVAL;
   if (cfg.max_pending == 0) cfg.max_pending = 1u << 18;
   if (cfg.max_pending > (1u << 24)) return MS_EINVAL;
-  if (cfg.mode != MS_SERVE_CONTINUOUS && cfg.mode != MS_SERVE_ONE_PER_LAUNCH) return MS_EINVAL;
+  if (cfg.mode != MS_SERVE_CONTINUOUS && cfg.mode != MS_SERVE_ONE_PER_LAUNCH && cfg.mode != MS_SERVE_ZERO_COPY)
+    return MS_EINVAL;
   const uint32_t S = (uint32_t)(cfg.staging_bytes / MS_PAGE_BYTES);
   if (cfg.max_wave_pages == 0) cfg.max_wave_pages = std::max<uint32_t>(1, S / cfg.waves_in_flight);
   if (cfg.max_request_pages == 0) cfg.max_request_pages = 4096;
@@ -456,7 +515,17 @@ int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_serv
   s->n_pages = n_pages;
   s->cfg = cfg;
   s->S = S;
+  s->idle_spin_ns = (uint64_t)cfg.idle_spin_us * 1000ull;
   DeviceGuard g(c->device);
+  if (cfg.mode == MS_SERVE_ZERO_COPY) {
+    void *dp = nullptr;
+    if (cudaHostGetDevicePointer(&dp, host_base, 0) != cudaSuccess || !dp) {
+      cudaGetLastError();
+      delete s;
+      return MS_EINVAL;  // the working set is not pinned, mapped host memory
+    }
+    s->d_host = (uint64_t)dp;
+  }
   cudaError_t e = cudaHostAlloc(&s->h_stage, (size_t)S * MS_PAGE_BYTES, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaHostAlloc(&s->h_ent, (size_t)S * sizeof(ms_page), cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_stage, (size_t)S * MS_PAGE_BYTES);
@@ -611,6 +680,8 @@ int ms_server_get_stats(const ms_server *s, ms_server_stats *out) {
   out->conflict_waits = s->st_conflict.load();
   out->budget_waits = s->st_budget.load();
   out->max_staged_pages = s->st_maxstaged.load();
+  out->gather_ns = s->st_gather_ns.load();
+  out->scatter_ns = s->st_scatter_ns.load();
   return MS_OK;
 }
 

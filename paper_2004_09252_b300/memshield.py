@@ -95,16 +95,17 @@ class ms_server_config(ctypes.Structure):
         ("mode", ctypes.c_uint32),
         ("zero_staging", ctypes.c_uint32),
         ("max_request_pages", ctypes.c_uint32),
+        ("idle_spin_us", ctypes.c_uint32),
     ]
 
 
 class ms_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("requests_done", "pages_done", "waves", "max_wave_requests",
                                                "max_wave_pages", "conflict_waits", "budget_waits",
-                                               "max_staged_pages")]
+                                               "max_staged_pages", "gather_ns", "scatter_ns")]
 
 
-MS_SERVE_CONTINUOUS, MS_SERVE_ONE_PER_LAUNCH = 0, 1
+MS_SERVE_CONTINUOUS, MS_SERVE_ONE_PER_LAUNCH, MS_SERVE_ZERO_COPY = 0, 1, 2
 
 
 def _load():
@@ -383,7 +384,8 @@ class Server:
 
     def __init__(self, ctx: Context, host_base, n_pages: int, *, staging_bytes: int = 0, max_wave_pages: int = 0,
                  waves_in_flight: int = 0, copy_threads: int | None = None, max_pending: int = 0,
-                 mode: int = MS_SERVE_CONTINUOUS, zero_staging: bool = False, max_request_pages: int = 0):
+                 mode: int = MS_SERVE_CONTINUOUS, zero_staging: bool = False, max_request_pages: int = 0,
+                 idle_spin_us: int | None = None):
         cfg = ms_server_config()
         _lib.ms_server_config_default(ctypes.byref(cfg))
         if staging_bytes:
@@ -400,6 +402,8 @@ class Server:
         cfg.zero_staging = 1 if zero_staging else 0
         if max_request_pages:
             cfg.max_request_pages = max_request_pages
+        if idle_spin_us is not None:
+            cfg.idle_spin_us = idle_spin_us
         h = ctypes.c_void_p()
         _check(_lib.ms_server_create(ctx.handle, _ptr(host_base), n_pages, ctypes.byref(cfg), ctypes.byref(h)),
                "ms_server_create")

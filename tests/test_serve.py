@@ -58,7 +58,7 @@ def test_submit_wait_matches_oracle(ms, key1):
     assert st["requests_done"] == len(reqs) and st["pages_done"] == len(touched)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_alone_equals_mix(ms, key1, mode):
     """Each request's result is identical when served alone (submit, wait, one
     at a time) and when served in a fast open-loop mix (bit-exact), and both
@@ -83,6 +83,8 @@ def test_alone_equals_mix(ms, key1, mode):
     assert np.array_equal(alone.numpy(), oracle_ws(key1, plain, pages))
     if mode == 1:
         assert st["max_wave_requests"] == 1 and st["waves"] == n_req
+    elif mode == 2:
+        assert st["gather_ns"] < st["waves"] * 10**6      # no staging copies in zero-copy mode
     else:
         assert st["waves"] <= n_req
 
@@ -146,3 +148,12 @@ def test_limits(ms, key1):
     with ms.Context(key1) as ctx:
         with pytest.raises(ms.MemShieldError):
             ms.Server(ctx, h, n, staging_bytes=1000)      # not a multiple of 4096
+
+
+def test_zero_copy_needs_pinned_memory(ms, key1):
+    import numpy as np
+    pageable = np.zeros(16 * PAGE, dtype=np.uint8)
+    with ms.Context(key1) as ctx:
+        with pytest.raises(ms.MemShieldError) as e:
+            ms.Server(ctx, pageable, 16, mode=ms.MS_SERVE_ZERO_COPY)
+        assert e.value.code == ms.MS_EINVAL
