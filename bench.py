@@ -172,6 +172,22 @@ class ClockSampler:
         return out
 
 
+# ----------------------------------------------------------- replicas (N>1)
+def aggregate_replicas(elapsed_ms: float, bytes_local: float, world: int, device="cpu"):
+    """Whole-job figures over independent replicas: the max elapsed time over
+    ranks and all ranks' bytes divided by it (GB/s).  With world == 1 this is
+    the local figure; with world > 1 it uses the default process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    b = torch.tensor([bytes_local], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    max_ms, total = float(t.item()), float(b.item())
+    return max_ms, total / (max_ms / 1e3) / 1e9
+
+
 # --------------------------------------------------------------- CPU oracle
 def cpu_oracle_rate(seconds: float, threads: int):
     """Time the CPU oracle (as it stands) on a bounded sample of the bulk buffer."""
@@ -264,13 +280,7 @@ def run_ours(args):
     if rc != 0:
         raise RuntimeError(f"ms_sync failed: {ms.strerror(rc)}")
     launch_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(2 * K)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    t = torch.tensor([total_ms], dtype=torch.float64, device=d.device)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    bytes_all = 2.0 * K * n * PAGE * world
-    value = bytes_all / (total_ms / 1e3) / 1e9
+    total_ms, value = aggregate_replicas(evs[0].elapsed_time(evs[-1]), 2.0 * K * n * PAGE, world, d.device)
     avg_launch_s = statistics.mean(launch_ms) / 1e3
 
     peaks, peaks_kind = load_peaks()
@@ -297,13 +307,10 @@ def run_ours(args):
             ctx.crypt_host(ms.MS_ENCRYPT, hbuf, 0, n, chunk, args.e2e_streams)
             ctx.crypt_host(ms.MS_DECRYPT, hbuf, 0, n, chunk, args.e2e_streams)
         barrier()
-        el = time.perf_counter() - t0
-        te = torch.tensor([el], dtype=torch.float64, device=d.device)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        el = float(te.item())
+        el_ms, e2e_gbs = aggregate_replicas((time.perf_counter() - t0) * 1e3, 2.0 * es * n * PAGE, world,
+                                            d.device)
         ok = np.array_equal(hbuf[:PAGE * 16].numpy(), plain[:PAGE * 16])
-        e2e = {"value": round(2.0 * es * n * PAGE * world / el / 1e9, 3), "unit": "GB/s",
+        e2e = {"value": round(e2e_gbs, 3), "unit": "GB/s",
                "h2d_bytes_per_step": 2 * n * PAGE, "d2h_bytes_per_step": 2 * n * PAGE,
                "steps": es, "chunk_bytes": chunk, "streams": args.e2e_streams or 2,
                "host_memory": "pinned", "round_trip_ok": bool(ok)}
@@ -599,7 +606,8 @@ def serve_rows(args, rates, modes, seconds):
                  "zero_copy": ms.MS_SERVE_ZERO_COPY}
         for name in modes:
             mode = modes[name]
-            with ms.Server(ctx, ws, n, mode=mode, copy_threads=args.copy_threads) as srv:
+            with ms.Server(ctx, ws, n, mode=mode, copy_threads=args.copy_threads,
+                           waves_in_flight=args.waves_in_flight, idle_spin_us=args.idle_spin_us) as srv:
                 lat, makespan = srv.replay(arrival, ops, offsets, pages, timeout_ms=600000)
                 st = srv.stats()
             total = int(offsets[-1])
@@ -685,6 +693,8 @@ def main():
     ap.add_argument("--serve-rates", type=lambda v: [float(x) for x in v.split(",")], default=SERVE_RATES)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--copy-threads", type=int, default=8)
+    ap.add_argument("--waves-in-flight", type=int, default=0, help="serving pipeline depth (0 = library default)")
+    ap.add_argument("--idle-spin-us", type=int, default=None, help="serving idle poll window (default: library's)")
     ap.add_argument("--serve-modes", type=lambda v: v.split(","), default=["continuous", "one_per_launch"])
     ap.add_argument("--batch-requests", type=lambda v: [int(x) for x in v.split(",")],
                     default=[1, 16, 256, 2000, 20000])

@@ -130,6 +130,8 @@ int ms_crypt_range(ms_ctx *ctx, int op, void *d_base, uint64_t first_page_id, si
  * last ms_sync, MS_ECUDA on a CUDA error.
  */
 int ms_sync(ms_ctx *ctx);
+/* ms_sync with its own bound instead of cfg.timeout_ms (0 = only check). */
+int ms_sync_for(ms_ctx *ctx, uint32_t timeout_ms);
 
 /*
  * Finish outstanding work (bounded), overwrite the device key with zeros and

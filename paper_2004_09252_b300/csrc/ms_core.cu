@@ -94,6 +94,7 @@ static void release(ms_ctx *c) {
     if (c->hs_buf[i]) cudaFree(c->hs_buf[i]);
   }
   if (c->sync_ev) cudaEventDestroy(c->sync_ev);
+  if (c->status_ev) cudaEventDestroy(c->status_ev);
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->d_status) cudaFree(c->d_status);
   if (c->d_key) cudaFree(c->d_key);
@@ -141,6 +142,7 @@ int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg_in) {
     c->own_stream = true;
   }
   MS_TRY(cudaEventCreateWithFlags(&c->sync_ev, cudaEventDisableTiming));
+  MS_TRY(cudaEventCreateWithFlags(&c->status_ev, cudaEventDisableTiming));
   MS_TRY(cudaMalloc(&c->d_status, sizeof(unsigned int)));
   MS_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream));
   MS_TRY(cudaHostAlloc(&c->h_status, sizeof(unsigned int), cudaHostAllocDefault));
@@ -267,18 +269,36 @@ int ms_crypt_range(ms_ctx *c, int op, void *d_base, uint64_t first_page_id, size
   return e == cudaSuccess ? MS_OK : cuda_fail(c, e);
 }
 
-int ms_sync(ms_ctx *c) {
+int ms_sync(ms_ctx *c) { return c ? ms_sync_for(c, c->cfg.timeout_ms) : MS_ENOTINIT; }
+
+int ms_sync_for(ms_ctx *c, uint32_t timeout_ms) {
   if (!c || !c->alive) return MS_ENOTINIT;
   std::lock_guard<std::mutex> lk(c->mu);
   DeviceGuard g(c->device);
-  cudaError_t e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(c->sync_ev, c->stream);
+  // A status read left unfinished by an earlier timed-out call is collected
+  // first, so no bad-entry report is lost.
+  if (c->status_pending) {
+    int rc = wait_event(c, c->status_ev, timeout_ms);
+    if (rc != MS_OK) return rc;
+    c->status_pending = false;
+    c->status_acc |= *(volatile unsigned int *)c->h_status;
+  }
+  // Phase 1: wait for the submitted work; a timeout here leaves nothing queued.
+  cudaError_t e = cudaEventRecord(c->sync_ev, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);
-  int rc = wait_event(c, c->sync_ev, c->cfg.timeout_ms);
+  int rc = wait_event(c, c->sync_ev, timeout_ms);
   if (rc != MS_OK) return rc;
-  const unsigned st = *(volatile unsigned int *)c->h_status;
-  *c->h_status = 0;
+  // Phase 2: read and clear the device status word.
+  e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(c->status_ev, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  c->status_pending = true;
+  rc = wait_event(c, c->status_ev, timeout_ms > 1000 ? timeout_ms : 1000);
+  if (rc != MS_OK) return rc;
+  c->status_pending = false;
+  const unsigned st = *(volatile unsigned int *)c->h_status | c->status_acc;
+  c->status_acc = 0;
   return (st & kStatusBadEntry) ? MS_EINVAL : MS_OK;
 }
 

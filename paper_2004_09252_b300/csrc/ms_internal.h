@@ -49,6 +49,9 @@ struct ms_ctx {
   unsigned int *d_status = nullptr;
   unsigned int *h_status = nullptr;  // pinned landing word for ms_sync
   cudaEvent_t sync_ev = nullptr;
+  cudaEvent_t status_ev = nullptr;   // the status-word read of ms_sync
+  bool status_pending = false;       // that read was queued but not yet collected
+  unsigned status_acc = 0;           // status bits collected by a call that then timed out
   ms::Tune tune;
   ms::QTune qtune;
   std::atomic<unsigned> tune_gen{0};  // bumped whenever tune/qtune change

@@ -127,6 +127,7 @@ def _load():
         "ms_decrypt_pages_dev": (I, [P, P, S]),
         "ms_crypt_range": (I, [P, I, P, U64, S]),
         "ms_sync": (I, [P]),
+        "ms_sync_for": (I, [P, ctypes.c_uint32]),
         "ms_shutdown": (I, [P]),
         "ms_strerror": (ctypes.c_char_p, [I]),
         "ms_last_cuda_error": (I, [P]),
@@ -290,6 +291,9 @@ class Context:
 
     def sync(self) -> int:
         return _lib.ms_sync(self.handle)
+
+    def sync_for(self, timeout_ms: int) -> int:
+        return _lib.ms_sync_for(self.handle, timeout_ms)
 
     def sync_checked(self) -> None:
         _check(self.sync(), "ms_sync")
