@@ -602,10 +602,10 @@ def serve_rows(args, rates, modes, seconds):
     for rate in rates:
         n_req = max(2000, int(rate / 8.0 * seconds))
         arrival, ops, offsets, pages = synth.serving_workload(5, n_req, rate, n)
-        modes = {"continuous": ms.MS_SERVE_CONTINUOUS, "one_per_launch": ms.MS_SERVE_ONE_PER_LAUNCH,
-                 "zero_copy": ms.MS_SERVE_ZERO_COPY}
+        mode_ids = {"continuous": ms.MS_SERVE_CONTINUOUS, "one_per_launch": ms.MS_SERVE_ONE_PER_LAUNCH,
+                    "zero_copy": ms.MS_SERVE_ZERO_COPY}
         for name in modes:
-            mode = modes[name]
+            mode = mode_ids[name]
             with ms.Server(ctx, ws, n, mode=mode, copy_threads=args.copy_threads,
                            waves_in_flight=args.waves_in_flight, idle_spin_us=args.idle_spin_us) as srv:
                 lat, makespan = srv.replay(arrival, ops, offsets, pages, timeout_ms=600000)

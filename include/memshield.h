@@ -307,7 +307,7 @@ typedef struct ms_server_config {
   uint32_t mode;             /* ms_serve_mode */
   uint32_t zero_staging;     /* nonzero: wipe staging pages after each wave */
   uint32_t max_request_pages;/* largest request accepted (default 4096; <= staging pages) */
-  uint32_t idle_spin_us;     /* idle server thread polls this long before sleeping (default 200) */
+  uint32_t idle_spin_us;     /* idle server thread polls this long before sleeping (default 2000) */
 } ms_server_config;
 
 typedef struct ms_server_stats {

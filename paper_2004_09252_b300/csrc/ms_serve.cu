@@ -468,7 +468,7 @@ void ms_server_config_default(ms_server_config *cfg) {
   cfg->max_pending = 1u << 18;
   cfg->mode = MS_SERVE_CONTINUOUS;
   cfg->max_request_pages = 4096;
-  cfg->idle_spin_us = 200;
+  cfg->idle_spin_us = 2000;
 }
 
 static void free_server(ms_server *s) {
