@@ -151,6 +151,11 @@ int ms_shutdown(ms_ctx *ctx);
  *                      + low halves): 2 all of them, 3 the 7s, 4 the 12s,
  *                      5 the 7s of column rounds, 6 the 7s through one wide
  *                      multiply, 7 the 12s and 7s of column rounds
+ *   hoist              1: the part of the first double round that does not
+ *                      depend on the block counter (41 of 992 operations) is
+ *                      computed once per page per thread and shared by its
+ *                      blocks; needs blocks_per_thread >= 2, dr_unroll =
+ *                      rounds / 2, rot_policy 0 or 1
  * ms_set_shape returns MS_EINVAL (and changes nothing) for a shape that is
  * not compiled for the context's round count.
  */
@@ -159,6 +164,7 @@ typedef struct ms_shape {
   uint32_t threads_per_cta;
   uint32_t dr_unroll;
   uint32_t rot_policy;
+  uint32_t hoist;
 } ms_shape;
 
 int ms_get_shape(const ms_ctx *ctx, ms_shape *out);

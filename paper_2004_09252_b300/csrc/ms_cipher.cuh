@@ -158,6 +158,112 @@ __device__ __forceinline__ void xor_block(uint4 *__restrict__ dst, const BlockSe
   __stcs(dst + 0, d0); __stcs(dst + 1, d1); __stcs(dst + 2, d2); __stcs(dst + 3, d3);
 }
 
+// The part of the first double round that is the same for all 64 blocks of a
+// page.  Only word 12 (the block counter) differs between them, and in the
+// first column round it enters only the quarter round on words (0, 4, 8, 12);
+// the other three column quarter rounds, the first add of that one, and the
+// counter-free steps of two diagonal quarter rounds depend on key and nonce
+// alone (41 of the 992 operations of a block).
+struct Prelude {
+  uint32_t a0;                                  // x0 + x4 (first step of column QR 0)
+  uint32_t x1, x2, x3, x5, x6, x7, x9, x10, x11, x13, x14, x15;  // after column QRs 1..3
+  uint32_t da1;                                 // diagonal QR (1,6,11,12): a = x1 + x6
+  uint32_t da2, dd2;                            // diagonal QR (2,7,8,13): a = x2 + x7, d = (x13 ^ a) <<< 16
+};
+
+template <int POL>
+__device__ __forceinline__ Prelude make_prelude(const BlockSeed &s, const MulConsts &mc) {
+  Prelude p;
+  uint32_t x1 = kSigma1, x2 = kSigma2, x3 = kSigma3;
+  uint32_t x5 = s.k[1], x6 = s.k[2], x7 = s.k[3];
+  uint32_t x9 = s.k[5], x10 = s.k[6], x11 = s.k[7];
+  uint32_t x13 = s.n0, x14 = s.n1, x15 = s.n2;
+  quarter_round<POL, true>(x1, x5, x9, x13, mc);
+  quarter_round<POL, true>(x2, x6, x10, x14, mc);
+  quarter_round<POL, true>(x3, x7, x11, x15, mc);
+  p.a0 = kSigma0 + s.k[0];
+  p.x1 = x1; p.x2 = x2; p.x3 = x3; p.x5 = x5; p.x6 = x6; p.x7 = x7;
+  p.x9 = x9; p.x10 = x10; p.x11 = x11; p.x13 = x13; p.x14 = x14; p.x15 = x15;
+  p.da1 = x1 + x6;
+  p.da2 = x2 + x7;
+  p.dd2 = rotl16<POL>(x13 ^ p.da2);
+  return p;
+}
+
+// xor_block with the first double round started from a Prelude.  The
+// remaining double rounds are fully unrolled.
+template <int ROUNDS, int POL>
+__device__ __forceinline__ void xor_block_hoisted(uint4 *__restrict__ dst, const BlockSeed &s, const Prelude &p,
+                                                  uint32_t counter, const MulConsts &mc) {
+  uint4 d0 = __ldcs(dst + 0), d1 = __ldcs(dst + 1), d2 = __ldcs(dst + 2), d3 = __ldcs(dst + 3);
+  uint32_t x0, x4, x8, x12;
+  uint32_t x1, x2, x3, x5 = p.x5, x6, x7, x9 = p.x9, x10 = p.x10, x11, x13, x14 = p.x14, x15 = p.x15;
+  {  // column QR (0, 4, 8, 12), the only one that sees the counter
+    uint32_t a = p.a0, b = s.k[0], c = s.k[4], d = counter;
+    d = rotl16<POL>(d ^ a);
+    c += d; b = rotl12<POL, true>(b ^ c, mc);
+    a += b; d = rotl8<POL>(d ^ a);
+    c += d; b = rotl7<POL, true>(b ^ c, mc);
+    x0 = a; x4 = b; x8 = c; x12 = d;
+  }
+  // diagonal round
+  quarter_round<POL, false>(x0, x5, x10, x15, mc);
+  {  // (1, 6, 11, 12): a = x1 + x6 precomputed
+    uint32_t a = p.da1, b = p.x6, c = p.x11, d = x12;
+    d = rotl16<POL>(d ^ a);
+    c += d; b = rotl12<POL, false>(b ^ c, mc);
+    a += b; d = rotl8<POL>(d ^ a);
+    c += d; b = rotl7<POL, false>(b ^ c, mc);
+    x1 = a; x6 = b; x11 = c; x12 = d;
+  }
+  {  // (2, 7, 8, 13): a = x2 + x7 and d = (x13 ^ a) <<< 16 precomputed
+    uint32_t a = p.da2, b = p.x7, c = x8, d = p.dd2;
+    c += d; b = rotl12<POL, false>(b ^ c, mc);
+    a += b; d = rotl8<POL>(d ^ a);
+    c += d; b = rotl7<POL, false>(b ^ c, mc);
+    x2 = a; x7 = b; x8 = c; x13 = d;
+  }
+  x3 = p.x3;
+  quarter_round<POL, false>(x3, x4, x9, x14, mc);
+#pragma unroll
+  for (int r = 1; r < ROUNDS / 2; ++r) {
+    quarter_round<POL, true>(x0, x4, x8, x12, mc);
+    quarter_round<POL, true>(x1, x5, x9, x13, mc);
+    quarter_round<POL, true>(x2, x6, x10, x14, mc);
+    quarter_round<POL, true>(x3, x7, x11, x15, mc);
+    quarter_round<POL, false>(x0, x5, x10, x15, mc);
+    quarter_round<POL, false>(x1, x6, x11, x12, mc);
+    quarter_round<POL, false>(x2, x7, x8, x13, mc);
+    quarter_round<POL, false>(x3, x4, x9, x14, mc);
+  }
+  d0.x ^= x0 + kSigma0;  d0.y ^= x1 + kSigma1;  d0.z ^= x2 + kSigma2;  d0.w ^= x3 + kSigma3;
+  d1.x ^= x4 + s.k[0];   d1.y ^= x5 + s.k[1];   d1.z ^= x6 + s.k[2];   d1.w ^= x7 + s.k[3];
+  d2.x ^= x8 + s.k[4];   d2.y ^= x9 + s.k[5];   d2.z ^= x10 + s.k[6];  d2.w ^= x11 + s.k[7];
+  d3.x ^= x12 + counter; d3.y ^= x13 + s.n0;    d3.z ^= x14 + s.n1;    d3.w ^= x15 + s.n2;
+  __stcs(dst + 0, d0); __stcs(dst + 1, d1); __stcs(dst + 2, d2); __stcs(dst + 3, d3);
+}
+
+// All blocks `t + b * TPP` (b < BPT) of one page for one thread; with HOIST the
+// counter-free prelude is computed once for them.
+template <int ROUNDS, int BPT, int UNR, int POL, bool HOIST>
+__device__ __forceinline__ void page_blocks(uint4 *__restrict__ pg, const BlockSeed &s, uint32_t t, uint32_t tpp,
+                                            const MulConsts &mc) {
+  if (HOIST) {
+    const Prelude p = make_prelude<POL>(s, mc);
+#pragma unroll 1
+    for (int b = 0; b < BPT; ++b) {
+      const uint32_t j = t + b * tpp;
+      xor_block_hoisted<ROUNDS, POL>(pg + 4 * j, s, p, j, mc);
+    }
+  } else {
+#pragma unroll 1
+    for (int b = 0; b < BPT; ++b) {
+      const uint32_t j = t + b * tpp;
+      xor_block<ROUNDS, UNR, POL>(pg + 4 * j, s, j, mc);
+    }
+  }
+}
+
 // Arguments shared by the page kernels.
 struct PageArgs {
   const ms_page *pages;   // entry list (list mode)
@@ -175,7 +281,7 @@ __device__ __forceinline__ bool entry_ok(uint64_t addr) { return addr != 0 && (a
 // K1, the one-launch bulk kernel.  Thread g works on page g / (64 / BPT) and,
 // inside it, on blocks t, t + 64/BPT, ... (t = g mod 64/BPT), so at each step
 // the threads of a warp touch consecutive 64-byte blocks of one page.
-template <int ROUNDS, int BPT, int UNR, int POL, bool RANGE>
+template <int ROUNDS, int BPT, int UNR, int POL, bool RANGE, bool HOIST = false>
 __global__ void __launch_bounds__(512) k_pages(const PageArgs a) {
   constexpr uint32_t TPP = 64 / BPT;  // threads per page
   const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -201,12 +307,7 @@ __global__ void __launch_bounds__(512) k_pages(const PageArgs a) {
   s.n0 = (uint32_t)pid;
   s.n1 = (uint32_t)(pid >> 32);
   s.n2 = a.domain;
-  uint4 *pg = reinterpret_cast<uint4 *>(addr);
-#pragma unroll 1
-  for (int b = 0; b < BPT; ++b) {
-    const uint32_t j = t + b * TPP;
-    xor_block<ROUNDS, UNR, POL>(pg + 4 * j, s, j, a.mc);
-  }
+  page_blocks<ROUNDS, BPT, UNR, POL, HOIST>(reinterpret_cast<uint4 *>(addr), s, t, TPP, a.mc);
 }
 
 // Arguments of the persistent queue kernel.
@@ -227,7 +328,7 @@ struct QueueArgs {
 // time (TPP = 64 / BPT threads per page), until the head passes the count.
 // The head only grows, so every CTA leaves after at most count / grab + 1
 // claims; nothing waits.
-template <int ROUNDS, int BPT, int UNR, int POL>
+template <int ROUNDS, int BPT, int UNR, int POL, bool HOIST = false>
 __global__ void __launch_bounds__(512) k_queue(const QueueArgs q) {
   constexpr uint32_t TPP = 64 / BPT;
   __shared__ uint32_t s_base;
@@ -253,12 +354,7 @@ __global__ void __launch_bounds__(512) k_queue(const QueueArgs q) {
       }
       s.n0 = (uint32_t)e.page_id;
       s.n1 = (uint32_t)(e.page_id >> 32);
-      uint4 *pg = reinterpret_cast<uint4 *>(e.addr);
-#pragma unroll 1
-      for (int b = 0; b < BPT; ++b) {
-        const uint32_t j = t + b * TPP;
-        xor_block<ROUNDS, UNR, POL>(pg + 4 * j, s, j, q.mc);
-      }
+      page_blocks<ROUNDS, BPT, UNR, POL, HOIST>(reinterpret_cast<uint4 *>(e.addr), s, t, TPP, q.mc);
     }
   }
 }

@@ -331,6 +331,7 @@ int ms_get_shape(const ms_ctx *c, ms_shape *out) {
   out->threads_per_cta = (uint32_t)c->tune.tpc;
   out->dr_unroll = (uint32_t)c->tune.unr;
   out->rot_policy = (uint32_t)c->tune.pol;
+  out->hoist = (uint32_t)c->tune.hoist;
   return MS_OK;
 }
 
@@ -342,6 +343,7 @@ int ms_set_shape(ms_ctx *c, const ms_shape *sh) {
   t.tpc = (int)sh->threads_per_cta;
   t.unr = (int)sh->dr_unroll;
   t.pol = (int)sh->rot_policy;
+  t.hoist = (int)sh->hoist;
   if (!shape_available((int)c->cfg.rounds, t)) return MS_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
   c->tune = t;

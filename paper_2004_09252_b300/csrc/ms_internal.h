@@ -19,6 +19,7 @@ struct Tune {
   int tpc = 256;     // threads per CTA
   int unr = 10;      // double rounds per loop trip
   int pol = kRotPerm;
+  int hoist = 0;     // counter-free prelude once per page per thread (needs bpt >= 2)
 };
 
 // Launch parameters of the persistent queue kernel (K2).

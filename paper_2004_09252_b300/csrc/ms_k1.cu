@@ -7,22 +7,25 @@ namespace {
 
 using LaunchFn = cudaError_t (*)(const PageArgs &, int, cudaStream_t);
 
-template <int R, int B, int U, int P, bool RG>
+template <int R, int B, int U, int P, bool RG, bool H>
 cudaError_t launch_k1(const PageArgs &a, int tpc, cudaStream_t s) {
   constexpr uint64_t TPP = 64 / B;
   const uint64_t threads = a.n_pages * TPP;
   const uint64_t grid = (threads + tpc - 1) / tpc;
   if (grid > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-  k_pages<R, B, U, P, RG><<<(unsigned)grid, tpc, 0, s>>>(a);
+  k_pages<R, B, U, P, RG, H><<<(unsigned)grid, tpc, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 struct Entry {
-  int rounds, bpt, unr, pol;
+  int rounds, bpt, unr, pol, hoist;
   LaunchFn list_fn, range_fn;
 };
 
-#define MS_K1(R, B, U, P) {R, B, U, P, &launch_k1<R, B, U, P, false>, &launch_k1<R, B, U, P, true>}
+#define MS_K1(R, B, U, P) {R, B, U, P, 0, &launch_k1<R, B, U, P, false, false>, &launch_k1<R, B, U, P, true, false>}
+// hoisted prelude; the remaining double rounds are always fully unrolled (unr = rounds / 2)
+#define MS_K1H(R, B, P) {R, B, R / 2, P, 1, &launch_k1<R, B, R / 2, P, false, true>, \
+                         &launch_k1<R, B, R / 2, P, true, true>}
 
 const Entry kTable[] = {
     // ChaCha20, the paper's cipher: the tuned search space.
@@ -40,6 +43,9 @@ const Entry kTable[] = {
     MS_K1(20, 1, 10, 5), MS_K1(20, 2, 10, 5), MS_K1(20, 4, 10, 5),
     MS_K1(20, 1, 10, 6), MS_K1(20, 2, 10, 6), MS_K1(20, 4, 10, 6),
     MS_K1(20, 1, 10, 7), MS_K1(20, 2, 10, 7), MS_K1(20, 4, 10, 7),
+    // counter-free part of the first double round computed once per page per thread
+    MS_K1H(20, 2, 1), MS_K1H(20, 4, 1), MS_K1H(20, 2, 0), MS_K1H(20, 4, 0),
+    MS_K1H(12, 2, 1), MS_K1H(12, 4, 1), MS_K1H(8, 2, 1), MS_K1H(8, 4, 1),
     // Reduced-round variants.
     MS_K1(12, 1, 6, 1), MS_K1(12, 2, 6, 1), MS_K1(12, 1, 2, 1),
     MS_K1(8, 1, 4, 1), MS_K1(8, 2, 4, 1), MS_K1(8, 1, 2, 1),
@@ -49,7 +55,7 @@ const Entry kTable[] = {
 
 const Entry *find(int rounds, const Tune &t) {
   for (const Entry &e : kTable)
-    if (e.rounds == rounds && e.bpt == t.bpt && e.unr == t.unr && e.pol == t.pol) return &e;
+    if (e.rounds == rounds && e.bpt == t.bpt && e.unr == t.unr && e.pol == t.pol && e.hoist == t.hoist) return &e;
   return nullptr;
 }
 
@@ -78,6 +84,7 @@ void k1_shape(int i, int *rounds, Tune *t) {
   t->bpt = kTable[i].bpt;
   t->unr = kTable[i].unr;
   t->pol = kTable[i].pol;
+  t->hoist = kTable[i].hoist;
 }
 
 }  // namespace ms

@@ -134,6 +134,7 @@ int ms_autotune(ms_ctx *c, size_t sample_pages, ms_tune_result *out) {
   r.shape.threads_per_cta = (uint32_t)best.tpc;
   r.shape.dr_unroll = (uint32_t)best.unr;
   r.shape.rot_policy = (uint32_t)best.pol;
+  r.shape.hoist = (uint32_t)best.hoist;
   r.k1_gbs = bytes / (best_ms * 1e-3) / 1e9;
 
   // ---- K2 over pages-per-claim and CTAs per SM, with the chosen shape
@@ -189,8 +190,8 @@ int ms_tune_save(const ms_ctx *c, const char *path) {
   FILE *f = std::fopen(path, "w");
   if (!f) return MS_EINVAL;
   const std::string tag = device_tag(c->device, c->sm_count);
-  std::fprintf(f, "memshield-tune-v1 %s %u %d %d %d %d %d %d\n", tag.c_str(), c->cfg.rounds, c->tune.bpt,
-               c->tune.tpc, c->tune.unr, c->tune.pol, c->qtune.grab, c->qtune.ctas_per_sm);
+  std::fprintf(f, "memshield-tune-v2 %s %u %d %d %d %d %d %d %d\n", tag.c_str(), c->cfg.rounds, c->tune.bpt,
+               c->tune.tpc, c->tune.unr, c->tune.pol, c->tune.hoist, c->qtune.grab, c->qtune.ctas_per_sm);
   std::fclose(f);
   return MS_OK;
 }
@@ -204,10 +205,10 @@ int ms_tune_load(ms_ctx *c, const char *path) {
   int sms, rounds;
   Tune t;
   QTune q;
-  const int got = std::fscanf(f, "%31s %255s %d %d %d %d %d %d %d %d", magic, name, &sms, &rounds, &t.bpt, &t.tpc,
-                              &t.unr, &t.pol, &q.grab, &q.ctas_per_sm);
+  const int got = std::fscanf(f, "%31s %255s %d %d %d %d %d %d %d %d %d", magic, name, &sms, &rounds, &t.bpt,
+                              &t.tpc, &t.unr, &t.pol, &t.hoist, &q.grab, &q.ctas_per_sm);
   std::fclose(f);
-  if (got != 10 || std::strcmp(magic, "memshield-tune-v1") != 0) return MS_EINVAL;
+  if (got != 11 || std::strcmp(magic, "memshield-tune-v2") != 0) return MS_EINVAL;
   const std::string tag = std::string(name) + " " + std::to_string(sms);
   if (tag != device_tag(c->device, c->sm_count) || rounds != (int)c->cfg.rounds) return MS_EINVAL;
   if (!shape_available(rounds, t) || q.grab < 1 || q.grab > 4096 || q.ctas_per_sm < 0) return MS_EINVAL;

@@ -53,6 +53,7 @@ class ms_shape(ctypes.Structure):
         ("threads_per_cta", ctypes.c_uint32),
         ("dr_unroll", ctypes.c_uint32),
         ("rot_policy", ctypes.c_uint32),
+        ("hoist", ctypes.c_uint32),
     ]
 
 
@@ -285,8 +286,9 @@ class Context:
         _check(_lib.ms_get_shape(self.handle, ctypes.byref(sh)), "ms_get_shape")
         return {f: getattr(sh, f) for f, _ in ms_shape._fields_}
 
-    def set_shape(self, blocks_per_thread: int, threads_per_cta: int, dr_unroll: int, rot_policy: int) -> None:
-        sh = ms_shape(blocks_per_thread, threads_per_cta, dr_unroll, rot_policy)
+    def set_shape(self, blocks_per_thread: int, threads_per_cta: int, dr_unroll: int, rot_policy: int,
+                  hoist: int = 0) -> None:
+        sh = ms_shape(blocks_per_thread, threads_per_cta, dr_unroll, rot_policy, hoist)
         _check(_lib.ms_set_shape(self.handle, ctypes.byref(sh)), "ms_set_shape")
 
     def sync(self) -> int:

@@ -54,15 +54,15 @@ def run_batched(ms, ctx, d, sizes, slots, ops, batch_requests, **bkw):
 
 
 @pytest.mark.parametrize("use_graph", [True, False])
-@pytest.mark.parametrize("bpt,tpc", [(1, 256), (2, 128), (4, 512)])
+@pytest.mark.parametrize("bpt,tpc,hoist", [(1, 256, 0), (2, 128, 0), (4, 512, 0), (4, 256, 1), (2, 512, 1)])
 @pytest.mark.parametrize("grab", [1, 7, 64])
-def test_batched_matches_oracle(ms, key1, use_graph, bpt, tpc, grab):
+def test_batched_matches_oracle(ms, key1, use_graph, bpt, tpc, hoist, grab):
     n_slots = 4096
     sizes, slots, ops = requests(40, n_slots, 120, 64)
     plain = synth.page_bytes_fast(41, 0, n_slots)
     d = torch.from_numpy(plain).cuda()
     with make_ctx(ms, key1) as ctx:
-        ctx.set_shape(bpt, tpc, 10, 1)
+        ctx.set_shape(bpt, tpc, 10, 1, hoist)
         st = run_batched(ms, ctx, d, sizes, slots, ops, batch_requests=17, use_graph=use_graph, grab=grab)
     want = oracle_expected(key1, plain, slots, slots)
     assert np.array_equal(d.cpu().numpy(), want)

@@ -66,10 +66,37 @@ def test_every_shape_scattered_ragged(ms, key1, bpt, unr, pol, tpc):
     with make_ctx(ms, key1) as ctx:
         ctx.set_shape(bpt, tpc, unr, pol)
         assert ctx.get_shape() == {"blocks_per_thread": bpt, "threads_per_cta": tpc, "dr_unroll": unr,
-                                   "rot_policy": pol}
+                                   "rot_policy": pol, "hoist": 0}
         ctx.encrypt_pages(pages)
         ctx.sync_checked()
     assert np.array_equal(d.cpu().numpy(), oracle_expected(key1, plain, slots, ids))
+
+
+@pytest.mark.parametrize("rounds,bpt,pol", [(20, 2, 1), (20, 4, 1), (20, 2, 0), (20, 4, 0), (12, 2, 1),
+                                            (12, 4, 1), (8, 2, 1), (8, 4, 1)])
+@pytest.mark.parametrize("tpc", [128, 512])
+def test_hoisted_prelude_shapes(ms, key1, rounds, bpt, pol, tpc):
+    """The shapes that compute the counter-free prelude once per page, in list and range mode."""
+    n_slots, n = 97, 61
+    plain = synth.page_bytes(17, 0, n_slots)
+    d = dev(plain)
+    slots = synth.scattered_slots(18, n_slots, n)
+    ids = (synth.splitmix64(19, 0, n)).astype(np.uint64)
+    with make_ctx(ms, key1, rounds=rounds, domain=77) as ctx:
+        ctx.set_shape(bpt, tpc, rounds // 2, pol, 1)
+        assert ctx.get_shape()["hoist"] == 1
+        ctx.encrypt_pages(ms.pages_array(d.data_ptr() + PAGE * slots.astype(np.uint64), ids))
+        ctx.sync_checked()
+        assert np.array_equal(d.cpu().numpy(), oracle_expected(key1, plain, slots, ids, domain=77, rounds=rounds))
+        r = dev(plain)
+        ctx.crypt_range(ms.MS_ENCRYPT, r, 1 << 40, n_slots)
+        ctx.sync_checked()
+        ids_r = (np.arange(n_slots, dtype=np.uint64) + np.uint64(1 << 40))
+        assert np.array_equal(r.cpu().numpy(), oracle_expected(key1, plain, np.arange(n_slots), ids_r, domain=77,
+                                                               rounds=rounds))
+    with make_ctx(ms, key1) as ctx:
+        with pytest.raises(ms.MemShieldError):
+            ctx.set_shape(1, 256, 10, 1, 1)         # hoisting needs >= 2 blocks per thread
 
 
 @pytest.mark.parametrize("rounds", [8, 12])
