@@ -188,6 +188,9 @@ int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg_in) {
   if (cfg.threads_per_cta) c->tune.tpc = (int)cfg.threads_per_cta;
   if (cfg.dr_unroll) c->tune.unr = (int)cfg.dr_unroll;
   if (cfg.rounds != 20 && !cfg.dr_unroll) c->tune.unr = (int)cfg.rounds / 2;
+  // the shared prelude needs >= 2 blocks per thread and a full unroll
+  if (c->tune.bpt < 2 || c->tune.unr != (int)cfg.rounds / 2) c->tune.hoist = 0;
+  if (!shape_available((int)cfg.rounds, c->tune)) c->tune.hoist = 0;
   if (!shape_available((int)cfg.rounds, c->tune)) {
     release(c);
     return MS_EINVAL;
