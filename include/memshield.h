@@ -69,6 +69,16 @@ typedef struct ms_page {
   uint64_t page_id; /* nonce words 13..14 (the paper's page address) */
 } ms_page;
 
+/* A page with its own domain word (the paper's client PID, nonce word 15),
+ * for callers that serve several clients through one context.  32 bytes. */
+typedef struct ms_page_dom {
+  uint64_t addr;     /* as in ms_page */
+  uint64_t page_id;  /* as in ms_page */
+  uint32_t domain;   /* nonce word 15 for this page (overrides ms_config.domain) */
+  uint32_t reserved0;
+  uint64_t reserved1;
+} ms_page_dom;
+
 typedef struct ms_ctx ms_ctx;
 
 typedef struct ms_config {
@@ -116,6 +126,15 @@ int ms_decrypt_pages(ms_ctx *ctx, const ms_page *pages, size_t n);
  */
 int ms_encrypt_pages_dev(ms_ctx *ctx, const ms_page *d_pages, size_t n);
 int ms_decrypt_pages_dev(ms_ctx *ctx, const ms_page *d_pages, size_t n);
+
+/*
+ * Per-page domain forms (Sec. 4.4: the seed includes the client's PID, so one
+ * GPU serves several clients with distinct keystreams).  Host list (checked
+ * and copied like ms_encrypt_pages) or device list (checked on the device).
+ * Encryption and decryption are the same call.
+ */
+int ms_crypt_pages_dom(ms_ctx *ctx, const ms_page_dom *pages, size_t n);
+int ms_crypt_pages_dom_dev(ms_ctx *ctx, const ms_page_dom *d_pages, size_t n);
 
 /*
  * Contiguous form: n_pages pages back to back at the device address d_base
@@ -338,13 +357,18 @@ int ms_server_create(ms_ctx *ctx, void *host_base, uint64_t n_pages, const ms_se
  * within the request, each < n_pages); *ticket identifies it.  MS_ERANGE: n
  * above max_request_pages; MS_EBUSY: max_pending tickets outstanding. */
 int ms_server_submit(ms_server *srv, int op, const uint64_t *page_index, uint32_t n, uint64_t *ticket);
+/* Same, for one client among several: its pages use `domain` as nonce word 15
+ * (the paper's PID) instead of the context's domain. */
+int ms_server_submit_dom(ms_server *srv, int op, uint32_t domain, const uint64_t *page_index, uint32_t n,
+                         uint64_t *ticket);
 /* 1 = done (its pages are back in the working set), 0 = pending, < 0 = error. */
 int ms_server_poll(ms_server *srv, uint64_t ticket);
 /* Wait up to timeout_ms for the ticket: MS_OK, MS_ETIMEDOUT or an error. */
 int ms_server_wait(ms_server *srv, uint64_t ticket, uint32_t timeout_ms);
 /*
- * Open-loop replay, for measurement: request r (op ops[r] on
- * page_index[offsets[r] .. offsets[r + 1])) is submitted at arrival_s[r]
+ * Open-loop replay, for measurement: request r (op ops[r], domain domains[r]
+ * or the context's when domains is NULL, on page_index[offsets[r] ..
+ * offsets[r + 1])) is submitted at arrival_s[r]
  * seconds after the start, however far behind the server is, and
  * latency_s[r] is its completion time minus that scheduled arrival (so
  * queueing delay counts: no coordinated omission).  *makespan_s receives the
@@ -352,9 +376,55 @@ int ms_server_wait(ms_server *srv, uint64_t ticket, uint32_t timeout_ms);
  * after the last arrival for completions.
  */
 int ms_server_replay(ms_server *srv, size_t n_requests, const double *arrival_s, const int *ops,
-                     const uint64_t *offsets, const uint64_t *page_index, double *latency_s,
-                     double *makespan_s, uint32_t timeout_ms);
+                     const uint32_t *domains, const uint64_t *offsets, const uint64_t *page_index,
+                     double *latency_s, double *makespan_s, uint32_t timeout_ms);
 int ms_server_get_stats(const ms_server *srv, ms_server_stats *out);
+
+/*
+ * ---- Sliding-window clients (the fault / eviction stream of Sec. 4.3) ----
+ *
+ * Each client owns working-set pages [first_page, first_page + n_pages), all
+ * ENCRYPTED (with the client's domain) when the run starts, and keeps a FIFO
+ * window of pages in clear.  For every access in its trace (page numbers
+ * relative to first_page):
+ *   - in the window: a hit;
+ *   - otherwise a fault: a one-page decrypt is submitted to the server and
+ *     the client waits for it (the faulting process is stalled), then the
+ *     page joins the window;
+ *   - when the window holds more than window_pages pages, its oldest
+ *     evict_batch pages are encrypted by one request the client does not
+ *     wait for (evict_batch = 1 is the paper's policy; larger batches evict
+ *     ahead of need, as the paper's future work suggests).
+ * Each client runs on its own thread; its requests use its domain (PID).
+ * At the end every eviction has completed; the pages still in a client's
+ * window are in clear and all its other pages are encrypted.
+ */
+typedef struct ms_window_config {
+  uint32_t window_pages;  /* maximum pages in clear per client (Table 1: 4, 8, 16, 32) */
+  uint32_t evict_batch;   /* pages encrypted per eviction request, 1..window_pages + 1 */
+} ms_window_config;
+
+typedef struct ms_window_client {
+  uint32_t domain;         /* the client's PID: nonce word 15 of its pages */
+  uint32_t reserved;
+  uint64_t first_page;     /* its pages in the server's working set (ranges must not overlap) */
+  uint64_t n_pages;
+  const uint64_t *trace;   /* accessed page numbers, each < n_pages */
+  uint64_t trace_len;
+} ms_window_client;
+
+typedef struct ms_window_stats {
+  uint64_t accesses, hits, faults, evictions, evict_requests;
+  uint64_t final_window_pages;
+  double fault_p50_us, fault_p99_us, fault_max_us;  /* fault service time seen by the client */
+  double elapsed_s;                                 /* the client's whole trace */
+} ms_window_stats;
+
+/* Run the clients to the end of their traces.  stats_out (may be NULL) gets one
+ * entry per client; final_window_out (may be NULL) gets window_pages + 1 slots
+ * per client with its final window, oldest first, padded with UINT64_MAX. */
+int ms_window_run(ms_server *srv, const ms_window_config *cfg, const ms_window_client *clients, size_t n_clients,
+                  ms_window_stats *stats_out, uint64_t *final_window_out, uint32_t timeout_ms);
 /* Drain (bounded), stop the threads and free.  NULL is a no-op. */
 int ms_server_destroy(ms_server *srv);
 

@@ -264,9 +264,17 @@ __device__ __forceinline__ void page_blocks(uint4 *__restrict__ pg, const BlockS
   }
 }
 
+// How K1 finds its pages.
+enum PageMode {
+  kModeList = 0,     // ms_page entries; domain from the context
+  kModeRange = 1,    // contiguous pages from `base`, ids first_id + k
+  kModeListDom = 2,  // ms_page_dom entries, each with its own domain word
+};
+
 // Arguments shared by the page kernels.
 struct PageArgs {
   const ms_page *pages;   // entry list (list mode)
+  const ms_page_dom *dpages;  // entry list with domains (list-domain mode)
   uint8_t *base;          // first page (range mode)
   uint64_t first_id;      // id of the first page (range mode)
   uint64_t n_pages;
@@ -281,7 +289,7 @@ __device__ __forceinline__ bool entry_ok(uint64_t addr) { return addr != 0 && (a
 // K1, the one-launch bulk kernel.  Thread g works on page g / (64 / BPT) and,
 // inside it, on blocks t, t + 64/BPT, ... (t = g mod 64/BPT), so at each step
 // the threads of a warp touch consecutive 64-byte blocks of one page.
-template <int ROUNDS, int BPT, int UNR, int POL, bool RANGE, bool HOIST = false>
+template <int ROUNDS, int BPT, int UNR, int POL, int MODE, bool HOIST = false>
 __global__ void __launch_bounds__(512) k_pages(const PageArgs a) {
   constexpr uint32_t TPP = 64 / BPT;  // threads per page
   const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -290,13 +298,21 @@ __global__ void __launch_bounds__(512) k_pages(const PageArgs a) {
   const uint32_t t = (uint32_t)(g % TPP);
 
   uint64_t addr, pid;
-  if (RANGE) {
+  uint32_t domain = a.domain;
+  if (MODE == kModeRange) {
     addr = (uint64_t)a.base + page * (uint64_t)MS_PAGE_BYTES;
     pid = a.first_id + page;
   } else {
-    const ms_page e = a.pages[page];
-    addr = e.addr;
-    pid = e.page_id;
+    if (MODE == kModeListDom) {
+      const ms_page_dom e = a.dpages[page];
+      addr = e.addr;
+      pid = e.page_id;
+      domain = e.domain;
+    } else {
+      const ms_page e = a.pages[page];
+      addr = e.addr;
+      pid = e.page_id;
+    }
     if (!entry_ok(addr)) {
       if (t == 0) atomicOr(a.status, kStatusBadEntry);
       return;
@@ -306,7 +322,7 @@ __global__ void __launch_bounds__(512) k_pages(const PageArgs a) {
   load_key(a.key, s.k);
   s.n0 = (uint32_t)pid;
   s.n1 = (uint32_t)(pid >> 32);
-  s.n2 = a.domain;
+  s.n2 = domain;
   page_blocks<ROUNDS, BPT, UNR, POL, HOIST>(reinterpret_cast<uint4 *>(addr), s, t, TPP, a.mc);
 }
 

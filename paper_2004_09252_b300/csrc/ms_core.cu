@@ -49,6 +49,67 @@ PageArgs make_args(const ms_ctx *c) {
   return a;
 }
 
+// Entry lists of either layout: ms_page (context domain) or ms_page_dom.
+template <typename E>
+void set_list(PageArgs &a, const E *p);
+template <>
+void set_list<ms_page>(PageArgs &a, const ms_page *p) { a.pages = p; }
+template <>
+void set_list<ms_page_dom>(PageArgs &a, const ms_page_dom *p) { a.dpages = p; }
+
+template <typename E>
+int submit_list_host(ms_ctx *c, const E *pages, size_t n) {
+  if (!c || !c->alive) return MS_ENOTINIT;
+  if (n == 0) return MS_OK;
+  if (!pages) return MS_EINVAL;
+  for (size_t i = 0; i < n; ++i)
+    if (pages[i].addr == 0 || (pages[i].addr & 15u)) return MS_EINVAL;
+  if (c->cfg.check_duplicates) {
+    std::unordered_set<uint64_t> seen;
+    seen.reserve(n * 2);
+    for (size_t i = 0; i < n; ++i)
+      if (!seen.insert(pages[i].addr).second) return MS_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  const size_t cap = c->cfg.list_capacity;  // slots hold cap entries of the larger layout
+  for (size_t off = 0; off < n; off += cap) {
+    const size_t cnt = std::min(cap, n - off);
+    ListSlot &s = c->slots[c->next_slot];
+    c->next_slot = (c->next_slot + 1) % kListSlots;
+    if (s.used) {
+      int rc = wait_event(c, s.done, c->cfg.timeout_ms);
+      if (rc != MS_OK) return rc;
+    }
+    std::memcpy(s.h, pages + off, cnt * sizeof(E));
+    cudaError_t e = cudaMemcpyAsync(s.d, s.h, cnt * sizeof(E), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    PageArgs a = make_args(c);
+    set_list<E>(a, static_cast<const E *>(s.d));
+    a.n_pages = cnt;
+    e = launch_pages(c, a, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    e = cudaEventRecord(s.done, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    s.used = true;
+  }
+  return MS_OK;
+}
+
+template <typename E>
+int submit_list_dev(ms_ctx *c, const E *d_pages, size_t n) {
+  if (!c || !c->alive) return MS_ENOTINIT;
+  if (n == 0) return MS_OK;
+  if (!d_pages || ((uintptr_t)d_pages & 15u)) return MS_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  PageArgs a = make_args(c);
+  set_list<E>(a, d_pages);
+  a.n_pages = n;
+  cudaError_t e = launch_pages(c, a, c->stream);
+  return e == cudaSuccess ? MS_OK : cuda_fail(c, e);
+}
+
 }  // namespace ms
 
 using namespace ms;
@@ -147,8 +208,8 @@ int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg_in) {
   MS_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream));
   MS_TRY(cudaHostAlloc(&c->h_status, sizeof(unsigned int), cudaHostAllocDefault));
   for (auto &s : c->slots) {
-    MS_TRY(cudaHostAlloc(&s.h, sizeof(ms_page) * cfg.list_capacity, cudaHostAllocDefault));
-    MS_TRY(cudaMalloc(&s.d, sizeof(ms_page) * cfg.list_capacity));
+    MS_TRY(cudaHostAlloc(&s.h, sizeof(ms_page_dom) * cfg.list_capacity, cudaHostAllocDefault));
+    MS_TRY(cudaMalloc(&s.d, sizeof(ms_page_dom) * cfg.list_capacity));
     MS_TRY(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
   }
 
@@ -200,62 +261,15 @@ int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg_in) {
   return MS_OK;
 }
 
-static int submit_list_host(ms_ctx *c, const ms_page *pages, size_t n) {
-  if (!c || !c->alive) return MS_ENOTINIT;
-  if (n == 0) return MS_OK;
-  if (!pages) return MS_EINVAL;
-  for (size_t i = 0; i < n; ++i)
-    if (pages[i].addr == 0 || (pages[i].addr & 15u)) return MS_EINVAL;
-  if (c->cfg.check_duplicates) {
-    std::unordered_set<uint64_t> seen;
-    seen.reserve(n * 2);
-    for (size_t i = 0; i < n; ++i)
-      if (!seen.insert(pages[i].addr).second) return MS_EINVAL;
-  }
-  std::lock_guard<std::mutex> lk(c->mu);
-  DeviceGuard g(c->device);
-  const size_t cap = c->cfg.list_capacity;
-  for (size_t off = 0; off < n; off += cap) {
-    const size_t cnt = std::min(cap, n - off);
-    ListSlot &s = c->slots[c->next_slot];
-    c->next_slot = (c->next_slot + 1) % kListSlots;
-    if (s.used) {
-      int rc = wait_event(c, s.done, c->cfg.timeout_ms);
-      if (rc != MS_OK) return rc;
-    }
-    std::memcpy(s.h, pages + off, cnt * sizeof(ms_page));
-    cudaError_t e = cudaMemcpyAsync(s.d, s.h, cnt * sizeof(ms_page), cudaMemcpyHostToDevice, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e);
-    PageArgs a = make_args(c);
-    a.pages = s.d;
-    a.n_pages = cnt;
-    e = launch_pages(c, a, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e);
-    e = cudaEventRecord(s.done, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e);
-    s.used = true;
-  }
-  return MS_OK;
-}
-
 int ms_encrypt_pages(ms_ctx *ctx, const ms_page *pages, size_t n) { return submit_list_host(ctx, pages, n); }
 int ms_decrypt_pages(ms_ctx *ctx, const ms_page *pages, size_t n) { return submit_list_host(ctx, pages, n); }
-
-static int submit_list_dev(ms_ctx *c, const ms_page *d_pages, size_t n) {
-  if (!c || !c->alive) return MS_ENOTINIT;
-  if (n == 0) return MS_OK;
-  if (!d_pages || ((uintptr_t)d_pages & 15u)) return MS_EINVAL;
-  std::lock_guard<std::mutex> lk(c->mu);
-  DeviceGuard g(c->device);
-  PageArgs a = make_args(c);
-  a.pages = d_pages;
-  a.n_pages = n;
-  cudaError_t e = launch_pages(c, a, c->stream);
-  return e == cudaSuccess ? MS_OK : cuda_fail(c, e);
-}
+int ms_crypt_pages_dom(ms_ctx *ctx, const ms_page_dom *pages, size_t n) { return submit_list_host(ctx, pages, n); }
 
 int ms_encrypt_pages_dev(ms_ctx *ctx, const ms_page *d_pages, size_t n) { return submit_list_dev(ctx, d_pages, n); }
 int ms_decrypt_pages_dev(ms_ctx *ctx, const ms_page *d_pages, size_t n) { return submit_list_dev(ctx, d_pages, n); }
+int ms_crypt_pages_dom_dev(ms_ctx *ctx, const ms_page_dom *d_pages, size_t n) {
+  return submit_list_dev(ctx, d_pages, n);
+}
 
 int ms_crypt_range(ms_ctx *c, int op, void *d_base, uint64_t first_page_id, size_t n_pages) {
   if (!c || !c->alive) return MS_ENOTINIT;

@@ -35,8 +35,8 @@ constexpr int kListSlots = 4;
 constexpr int kMaxHostStreams = 4;
 
 struct ListSlot {
-  ms_page *h = nullptr;  // pinned copy of a host entry list
-  ms_page *d = nullptr;  // device copy read by the kernel
+  void *h = nullptr;  // pinned copy of a host entry list (room for list_capacity ms_page_dom)
+  void *d = nullptr;  // device copy read by the kernel
   cudaEvent_t done = nullptr;
   bool used = false;
 };

@@ -1,5 +1,6 @@
 // K1 variant table: every compiled (rounds, blocks/thread, unroll, rotation
-// policy, list|range) instance of the bulk page kernel, and its launcher.
+// policy, prelude) instance of the bulk page kernel, each in its three entry
+// modes (list, range, list with per-entry domain), and its launcher.
 #include "ms_internal.h"
 
 namespace ms {
@@ -7,25 +8,30 @@ namespace {
 
 using LaunchFn = cudaError_t (*)(const PageArgs &, int, cudaStream_t);
 
-template <int R, int B, int U, int P, bool RG, bool H>
+template <int R, int B, int U, int P, int M, bool H>
 cudaError_t launch_k1(const PageArgs &a, int tpc, cudaStream_t s) {
   constexpr uint64_t TPP = 64 / B;
   const uint64_t threads = a.n_pages * TPP;
   const uint64_t grid = (threads + tpc - 1) / tpc;
   if (grid > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-  k_pages<R, B, U, P, RG, H><<<(unsigned)grid, tpc, 0, s>>>(a);
+  k_pages<R, B, U, P, M, H><<<(unsigned)grid, tpc, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 struct Entry {
   int rounds, bpt, unr, pol, hoist;
-  LaunchFn list_fn, range_fn;
+  LaunchFn fn[3];  // indexed by PageMode
 };
 
-#define MS_K1(R, B, U, P) {R, B, U, P, 0, &launch_k1<R, B, U, P, false, false>, &launch_k1<R, B, U, P, true, false>}
+#define MS_K1(R, B, U, P)                                                                          \
+  {R, B, U, P, 0,                                                                                  \
+   {&launch_k1<R, B, U, P, kModeList, false>, &launch_k1<R, B, U, P, kModeRange, false>,           \
+    &launch_k1<R, B, U, P, kModeListDom, false>}}
 // hoisted prelude; the remaining double rounds are always fully unrolled (unr = rounds / 2)
-#define MS_K1H(R, B, P) {R, B, R / 2, P, 1, &launch_k1<R, B, R / 2, P, false, true>, \
-                         &launch_k1<R, B, R / 2, P, true, true>}
+#define MS_K1H(R, B, P)                                                                            \
+  {R, B, R / 2, P, 1,                                                                              \
+   {&launch_k1<R, B, R / 2, P, kModeList, true>, &launch_k1<R, B, R / 2, P, kModeRange, true>,     \
+    &launch_k1<R, B, R / 2, P, kModeListDom, true>}}
 
 const Entry kTable[] = {
     // ChaCha20, the paper's cipher: the tuned search space.
@@ -70,11 +76,12 @@ cudaError_t launch_pages_shape(const PageArgs &a, int rounds, const Tune &t, boo
   const Entry *e = find(rounds, t);
   if (!e) return cudaErrorInvalidValue;
   if (a.n_pages == 0) return cudaSuccess;
-  return (range ? e->range_fn : e->list_fn)(a, t.tpc, s);
+  const int mode = range ? kModeRange : (a.dpages ? kModeListDom : kModeList);
+  return e->fn[mode](a, t.tpc, s);
 }
 
 cudaError_t launch_pages(const ms_ctx *c, const PageArgs &a, cudaStream_t s) {
-  return launch_pages_shape(a, (int)c->cfg.rounds, c->tune, a.pages == nullptr, s);
+  return launch_pages_shape(a, (int)c->cfg.rounds, c->tune, a.pages == nullptr && a.dpages == nullptr, s);
 }
 
 // Every compiled shape, for the autotuner.

@@ -49,6 +49,7 @@ struct Req {
   std::atomic<int> error{0};
   std::atomic<uint64_t> ticket{~0ull};
   int op = 0;
+  uint32_t domain = 0;         // nonce word 15 of this request's pages
   std::vector<uint64_t> pages;
   uint64_t t_sched_ns = 0;     // arrival time latency is measured from
   std::atomic<uint64_t> t_done_ns{0};
@@ -153,7 +154,7 @@ struct ms_server {
   ms_server_config cfg{};
   uint32_t S = 0;  // staging slots
   uint8_t *h_stage = nullptr, *d_stage = nullptr;
-  ms_page *h_ent = nullptr, *d_ent = nullptr;
+  ms_page_dom *h_ent = nullptr, *d_ent = nullptr;
   cudaStream_t s_in = nullptr, s_work[2] = {nullptr, nullptr};
   std::vector<Req> reqs;
   std::mutex qmu;
@@ -284,7 +285,10 @@ int ms_server::issue(Wave &w) {
   for (uint64_t t : w.tickets) {
     Req &r = slot(t);
     r.state.store(kAdmitted, std::memory_order_release);
-    for (uint64_t pg : r.pages) map.push_back({pg, k++});
+    for (uint64_t pg : r.pages) {
+      h_ent[k].domain = r.domain;
+      map.push_back({pg, k++});
+    }
   }
   const bool zc = cfg.mode == MS_SERVE_ZERO_COPY;
   const uint64_t tg = now_ns();
@@ -308,12 +312,12 @@ int ms_server::issue(Wave &w) {
   cudaError_t e = cudaSuccess;
   if (!zc) e = cudaMemcpyAsync(d_stage + off, h_stage + off, bytes, cudaMemcpyHostToDevice, s_in);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_ent + w.pos, h_ent + w.pos, sizeof(ms_page) * w.len, cudaMemcpyHostToDevice, s_in);
+    e = cudaMemcpyAsync(d_ent + w.pos, h_ent + w.pos, sizeof(ms_page_dom) * w.len, cudaMemcpyHostToDevice, s_in);
   if (e == cudaSuccess) e = cudaEventRecord(w.ev_h2d, s_in);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(sw, w.ev_h2d, 0);
   if (e == cudaSuccess) {
     PageArgs a = make_args(ctx);
-    a.pages = d_ent + w.pos;
+    a.dpages = d_ent + w.pos;
     a.n_pages = w.len;
     e = launch_pages(ctx, a, sw);
   }
@@ -527,9 +531,9 @@ int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_serv
     s->d_host = (uint64_t)dp;
   }
   cudaError_t e = cudaHostAlloc(&s->h_stage, (size_t)S * MS_PAGE_BYTES, cudaHostAllocDefault);
-  if (e == cudaSuccess) e = cudaHostAlloc(&s->h_ent, (size_t)S * sizeof(ms_page), cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc(&s->h_ent, (size_t)S * sizeof(ms_page_dom), cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaMalloc(&s->d_stage, (size_t)S * MS_PAGE_BYTES);
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_ent, (size_t)S * sizeof(ms_page));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_ent, (size_t)S * sizeof(ms_page_dom));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_work[0], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_work[1], cudaStreamNonBlocking);
@@ -550,8 +554,8 @@ int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_serv
   return MS_OK;
 }
 
-static int submit_internal(ms_server *s, int op, const uint64_t *page_index, uint32_t n, uint64_t *ticket,
-                           uint64_t t_sched, double *lat_out) {
+static int submit_internal(ms_server *s, int op, uint32_t domain, const uint64_t *page_index, uint32_t n,
+                           uint64_t *ticket, uint64_t t_sched, double *lat_out) {
   if (!s) return MS_EINVAL;
   if (op != MS_ENCRYPT && op != MS_DECRYPT) return MS_EINVAL;
   if (n == 0 || !page_index) return MS_EINVAL;
@@ -575,6 +579,7 @@ static int submit_internal(ms_server *s, int op, const uint64_t *page_index, uin
   r.ticket.store(t);  // before next_ticket: a poll that sees ticket t valid finds the slot claimed
   s->next_ticket.store(t + 1);
   r.op = op;
+  r.domain = domain;
   r.pages.assign(page_index, page_index + n);
   r.error.store(0);
   r.t_done_ns.store(0);
@@ -588,7 +593,13 @@ static int submit_internal(ms_server *s, int op, const uint64_t *page_index, uin
 }
 
 int ms_server_submit(ms_server *s, int op, const uint64_t *page_index, uint32_t n, uint64_t *ticket) {
-  return submit_internal(s, op, page_index, n, ticket, 0, nullptr);
+  if (!s) return MS_EINVAL;
+  return submit_internal(s, op, s->ctx->cfg.domain, page_index, n, ticket, 0, nullptr);
+}
+
+int ms_server_submit_dom(ms_server *s, int op, uint32_t domain, const uint64_t *page_index, uint32_t n,
+                         uint64_t *ticket) {
+  return submit_internal(s, op, domain, page_index, n, ticket, 0, nullptr);
 }
 
 int ms_server_poll(ms_server *s, uint64_t ticket) {
@@ -619,8 +630,9 @@ int ms_server_wait(ms_server *s, uint64_t ticket, uint32_t timeout_ms) {
   }
 }
 
-int ms_server_replay(ms_server *s, size_t n, const double *arrival_s, const int *ops, const uint64_t *offsets,
-                     const uint64_t *page_index, double *latency_s, double *makespan_s, uint32_t timeout_ms) {
+int ms_server_replay(ms_server *s, size_t n, const double *arrival_s, const int *ops, const uint32_t *domains,
+                     const uint64_t *offsets, const uint64_t *page_index, double *latency_s, double *makespan_s,
+                     uint32_t timeout_ms) {
   if (!s || (n && (!arrival_s || !ops || !offsets || !page_index || !latency_s))) return MS_EINVAL;
   for (size_t r = 0; r < n; ++r) latency_s[r] = -1.0;
   // precise pacing: short timer slack for this thread while replaying
@@ -644,7 +656,9 @@ int ms_server_replay(ms_server *s, size_t n, const double *arrival_s, const int 
     const uint64_t n_pg = offsets[r + 1] - offsets[r];
     const uint64_t spin_limit = now_ns() + (uint64_t)timeout_ms * 1000000ull;
     for (;;) {
-      int rc = submit_internal(s, ops[r], page_index + offsets[r], (uint32_t)n_pg, &tickets[r], target, &latency_s[r]);
+      const uint32_t dom = domains ? domains[r] : s->ctx->cfg.domain;
+      int rc = submit_internal(s, ops[r], dom, page_index + offsets[r], (uint32_t)n_pg, &tickets[r], target,
+                               &latency_s[r]);
       if (rc == MS_OK) break;
       if (rc != MS_EBUSY) return rc;
       if (now_ns() > spin_limit) return MS_ETIMEDOUT;

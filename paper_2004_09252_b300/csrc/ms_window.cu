@@ -1,0 +1,150 @@
+// Sliding-window client driver: produces the paper's fault / eviction stream
+// (Sec. 4.3) from page-access traces and serves it through an ms_server.
+//
+// Each client owns a range of working-set pages, all encrypted at the start,
+// and a FIFO window of pages in clear.  An access to a page outside the
+// window is a fault: the client submits a one-page decrypt and waits for it
+// (the faulting thread is stalled until the page is resolved), then appends
+// the page to its window.  When the window grows past its maximum, the
+// oldest pages are evicted: one encrypt request for `evict_batch` of them,
+// which the client does not wait for (a later fault on one of those pages
+// waits for its encryption through the server's in-flight rule).  Clients
+// run on their own threads with their own domain (the paper's PID).
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <thread>
+#include <unordered_set>
+#include <vector>
+
+#include "ms_internal.h"
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct ClientRun {
+  const ms_window_client *cl;
+  ms_window_stats st{};
+  std::vector<double> lat_us;
+  std::vector<uint64_t> final_window;
+  std::vector<uint64_t> evict_tickets;
+  int rc = MS_OK;
+};
+
+void run_client(ms_server *srv, const ms_window_config &cfg, ClientRun &cr, uint32_t timeout_ms) {
+  const ms_window_client &cl = *cr.cl;
+  std::deque<uint64_t> window;  // working-set page indices in clear, oldest first
+  std::unordered_set<uint64_t> in_window;
+  cr.lat_us.reserve(cl.trace_len / 4 + 16);
+  const auto t0 = clk::now();
+  for (size_t i = 0; i < cl.trace_len; ++i) {
+    const uint64_t rel = cl.trace[i];
+    if (rel >= cl.n_pages) {
+      cr.rc = MS_EINVAL;
+      return;
+    }
+    const uint64_t pg = cl.first_page + rel;
+    cr.st.accesses += 1;
+    if (in_window.count(pg)) {
+      cr.st.hits += 1;
+      continue;
+    }
+    // fault: decrypt the page and wait for it
+    const auto f0 = clk::now();
+    uint64_t ticket;
+    int rc;
+    for (;;) {
+      rc = ms_server_submit_dom(srv, MS_DECRYPT, cl.domain, &pg, 1, &ticket);
+      if (rc != MS_EBUSY) break;
+      std::this_thread::yield();
+    }
+    if (rc == MS_OK) rc = ms_server_wait(srv, ticket, timeout_ms);
+    if (rc != MS_OK) {
+      cr.rc = rc;
+      return;
+    }
+    cr.lat_us.push_back(std::chrono::duration<double, std::micro>(clk::now() - f0).count());
+    cr.st.faults += 1;
+    window.push_back(pg);
+    in_window.insert(pg);
+    if (window.size() > cfg.window_pages) {
+      const size_t k = std::min<size_t>(cfg.evict_batch, window.size());
+      std::vector<uint64_t> ev(window.begin(), window.begin() + (long)k);
+      window.erase(window.begin(), window.begin() + (long)k);
+      for (uint64_t e : ev) in_window.erase(e);
+      for (;;) {
+        rc = ms_server_submit_dom(srv, MS_ENCRYPT, cl.domain, ev.data(), (uint32_t)k, &ticket);
+        if (rc != MS_EBUSY) break;
+        std::this_thread::yield();
+      }
+      if (rc != MS_OK) {
+        cr.rc = rc;
+        return;
+      }
+      cr.st.evictions += k;
+      cr.st.evict_requests += 1;
+      cr.evict_tickets.push_back(ticket);
+    }
+  }
+  // the client's evictions complete before it reports
+  for (uint64_t t : cr.evict_tickets) {
+    const int rc = ms_server_wait(srv, t, timeout_ms);
+    if (rc != MS_OK) {
+      cr.rc = rc;
+      return;
+    }
+  }
+  cr.st.elapsed_s = std::chrono::duration<double>(clk::now() - t0).count();
+  cr.final_window.assign(window.begin(), window.end());
+}
+
+double percentile(std::vector<double> v, double q) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  const double pos = q * (double)(v.size() - 1);
+  const size_t lo = (size_t)pos;
+  const size_t hi = std::min(v.size() - 1, lo + 1);
+  return v[lo] + (v[hi] - v[lo]) * (pos - (double)lo);
+}
+
+}  // namespace
+
+extern "C" int ms_window_run(ms_server *srv, const ms_window_config *cfg, const ms_window_client *clients,
+                             size_t n_clients, ms_window_stats *stats_out, uint64_t *final_window_out,
+                             uint32_t timeout_ms) {
+  if (!srv || !cfg || (n_clients && !clients)) return MS_EINVAL;
+  if (cfg->window_pages == 0 || cfg->evict_batch == 0 || cfg->evict_batch > cfg->window_pages + 1) return MS_EINVAL;
+  for (size_t c = 0; c < n_clients; ++c) {
+    if (!clients[c].trace && clients[c].trace_len) return MS_EINVAL;
+    for (size_t d = 0; d < c; ++d) {  // clients own disjoint page ranges
+      const ms_window_client &a = clients[c], &b = clients[d];
+      if (a.first_page < b.first_page + b.n_pages && b.first_page < a.first_page + a.n_pages) return MS_EINVAL;
+    }
+  }
+  std::vector<ClientRun> runs(n_clients);
+  std::vector<std::thread> th;
+  for (size_t c = 0; c < n_clients; ++c) {
+    runs[c].cl = &clients[c];
+    th.emplace_back([&, c] { run_client(srv, *cfg, runs[c], timeout_ms); });
+  }
+  for (auto &t : th) t.join();
+  int rc = MS_OK;
+  for (size_t c = 0; c < n_clients; ++c) {
+    ClientRun &r = runs[c];
+    if (r.rc != MS_OK && rc == MS_OK) rc = r.rc;
+    r.st.fault_p50_us = percentile(r.lat_us, 0.50);
+    r.st.fault_p99_us = percentile(r.lat_us, 0.99);
+    r.st.fault_max_us = r.lat_us.empty() ? 0.0 : *std::max_element(r.lat_us.begin(), r.lat_us.end());
+    r.st.final_window_pages = r.final_window.size();
+    if (stats_out) stats_out[c] = r.st;
+    if (final_window_out) {
+      // client c's final window goes to final_window_out[c * (window_pages + 1) ...], oldest first
+      uint64_t *dst = final_window_out + c * ((size_t)cfg->window_pages + 1);
+      for (size_t i = 0; i < (size_t)cfg->window_pages + 1; ++i)
+        dst[i] = i < r.final_window.size() ? r.final_window[i] : ~0ull;
+    }
+  }
+  return rc;
+}

@@ -23,6 +23,8 @@ MS_ENCRYPT, MS_DECRYPT = 0, 1
 MS_NOALLOC_MAX_PAGES = 16384
 
 PAGE_DTYPE = np.dtype([("addr", "<u8"), ("page_id", "<u8")])
+PAGE_DOM_DTYPE = np.dtype([("addr", "<u8"), ("page_id", "<u8"), ("domain", "<u4"), ("reserved0", "<u4"),
+                           ("reserved1", "<u8")])
 
 
 class MemShieldError(RuntimeError):
@@ -109,6 +111,21 @@ class ms_server_stats(ctypes.Structure):
 MS_SERVE_CONTINUOUS, MS_SERVE_ONE_PER_LAUNCH, MS_SERVE_ZERO_COPY = 0, 1, 2
 
 
+class ms_window_config(ctypes.Structure):
+    _fields_ = [("window_pages", ctypes.c_uint32), ("evict_batch", ctypes.c_uint32)]
+
+
+class ms_window_client(ctypes.Structure):
+    _fields_ = [("domain", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("first_page", ctypes.c_uint64),
+                ("n_pages", ctypes.c_uint64), ("trace", ctypes.c_void_p), ("trace_len", ctypes.c_uint64)]
+
+
+class ms_window_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("accesses", "hits", "faults", "evictions", "evict_requests",
+                                               "final_window_pages")] + \
+               [(n, ctypes.c_double) for n in ("fault_p50_us", "fault_p99_us", "fault_max_us", "elapsed_s")]
+
+
 def _load():
     path = _build.LIB
     if not os.path.exists(path):
@@ -149,7 +166,12 @@ def _load():
         "ms_server_submit": (I, [P, I, P, ctypes.c_uint32, ctypes.POINTER(U64)]),
         "ms_server_poll": (I, [P, U64]),
         "ms_server_wait": (I, [P, U64, ctypes.c_uint32]),
-        "ms_server_replay": (I, [P, S, P, P, P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.c_uint32]),
+        "ms_server_replay": (I, [P, S, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.c_uint32]),
+        "ms_server_submit_dom": (I, [P, I, ctypes.c_uint32, P, ctypes.c_uint32, ctypes.POINTER(U64)]),
+        "ms_crypt_pages_dom": (I, [P, P, S]),
+        "ms_window_run": (I, [P, ctypes.POINTER(ms_window_config), ctypes.POINTER(ms_window_client), S,
+                              ctypes.POINTER(ms_window_stats), P, ctypes.c_uint32]),
+        "ms_crypt_pages_dom_dev": (I, [P, P, S]),
         "ms_server_get_stats": (I, [P, ctypes.POINTER(ms_server_stats)]),
         "ms_server_destroy": (I, [P]),
         "ms_tune_save": (I, [P, ctypes.c_char_p]),
@@ -192,6 +214,15 @@ def _ptr(x) -> int:
     if isinstance(x, np.ndarray):
         return x.ctypes.data
     raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def pages_dom_array(addrs, page_ids, domains) -> np.ndarray:
+    """Pack (addr, page_id, domain) triples into the 32-byte ms_page_dom layout."""
+    a = np.zeros(len(addrs), dtype=PAGE_DOM_DTYPE)
+    a["addr"] = np.asarray(addrs, dtype=np.uint64)
+    a["page_id"] = np.asarray(page_ids, dtype=np.uint64)
+    a["domain"] = np.asarray(domains, dtype=np.uint32)
+    return a
 
 
 def pages_array(addrs, page_ids) -> np.ndarray:
@@ -251,6 +282,13 @@ class Context:
 
     def decrypt_pages_dev(self, d_pages, n: int) -> None:
         _check(_lib.ms_decrypt_pages_dev(self.handle, _ptr(d_pages), n), "ms_decrypt_pages_dev")
+
+    def crypt_pages_dom(self, pages: np.ndarray) -> None:
+        pages = np.ascontiguousarray(pages, dtype=PAGE_DOM_DTYPE)
+        _check(_lib.ms_crypt_pages_dom(self.handle, pages.ctypes.data, pages.size), "ms_crypt_pages_dom")
+
+    def crypt_pages_dom_dev(self, d_pages, n: int) -> None:
+        _check(_lib.ms_crypt_pages_dom_dev(self.handle, _ptr(d_pages), n), "ms_crypt_pages_dom_dev")
 
     def crypt_range(self, op: int, d_base, first_page_id: int, n_pages: int) -> None:
         _check(_lib.ms_crypt_range(self.handle, op, _ptr(d_base), first_page_id, n_pages), "ms_crypt_range")
@@ -416,10 +454,14 @@ class Server:
         self.handle = h.value
         self.ctx = ctx
 
-    def submit(self, op: int, page_index) -> int:
+    def submit(self, op: int, page_index, domain: int | None = None) -> int:
         idx = np.ascontiguousarray(page_index, dtype=np.uint64)
         t = ctypes.c_uint64()
-        _check(_lib.ms_server_submit(self.handle, op, idx.ctypes.data, idx.size, ctypes.byref(t)), "ms_server_submit")
+        if domain is None:
+            rc = _lib.ms_server_submit(self.handle, op, idx.ctypes.data, idx.size, ctypes.byref(t))
+        else:
+            rc = _lib.ms_server_submit_dom(self.handle, op, domain, idx.ctypes.data, idx.size, ctypes.byref(t))
+        _check(rc, "ms_server_submit")
         return t.value
 
     def poll(self, ticket: int) -> int:
@@ -428,18 +470,41 @@ class Server:
     def wait(self, ticket: int, timeout_ms: int = 10000) -> None:
         _check(_lib.ms_server_wait(self.handle, ticket, timeout_ms), "ms_server_wait")
 
-    def replay(self, arrival_s, ops, offsets, page_index, timeout_ms: int = 60000):
+    def replay(self, arrival_s, ops, offsets, page_index, timeout_ms: int = 60000, domains=None):
         """Open-loop replay; returns (latency_s array, makespan_s)."""
         arrival_s = np.ascontiguousarray(arrival_s, dtype=np.float64)
         ops = np.ascontiguousarray(ops, dtype=np.int32)
+        dom = None if domains is None else np.ascontiguousarray(domains, dtype=np.uint32)
         offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
         page_index = np.ascontiguousarray(page_index, dtype=np.uint64)
         lat = np.empty(arrival_s.size, dtype=np.float64)
         mk = ctypes.c_double()
         _check(_lib.ms_server_replay(self.handle, arrival_s.size, arrival_s.ctypes.data, ops.ctypes.data,
+                                     None if dom is None else dom.ctypes.data,
                                      offsets.ctypes.data, page_index.ctypes.data, lat.ctypes.data,
                                      ctypes.byref(mk), timeout_ms), "ms_server_replay")
         return lat, mk.value
+
+    def run_window_clients(self, window_pages: int, evict_batch: int, clients, timeout_ms: int = 60000):
+        """Sliding-window clients: `clients` is a list of (domain, first_page, n_pages, trace).
+        Returns (per-client stats dicts, per-client final windows as lists of page indices)."""
+        cfg = ms_window_config(window_pages, evict_batch)
+        arr = (ms_window_client * len(clients))()
+        keep = []
+        for i, (dom, first, n, trace) in enumerate(clients):
+            tr = np.ascontiguousarray(trace, dtype=np.uint64)
+            keep.append(tr)
+            arr[i] = ms_window_client(dom, 0, first, n, tr.ctypes.data, tr.size)
+        st = (ms_window_stats * len(clients))()
+        fw = np.empty(len(clients) * (window_pages + 1), dtype=np.uint64)
+        _check(_lib.ms_window_run(self.handle, ctypes.byref(cfg), arr, len(clients), st, fw.ctypes.data, timeout_ms),
+               "ms_window_run")
+        stats = [{f: getattr(st[i], f) for f, _ in ms_window_stats._fields_} for i in range(len(clients))]
+        wins = []
+        for i in range(len(clients)):
+            w = fw[i * (window_pages + 1):(i + 1) * (window_pages + 1)]
+            wins.append([int(x) for x in w if x != np.uint64(0xFFFFFFFFFFFFFFFF)])
+        return stats, wins
 
     def stats(self) -> dict:
         st = ms_server_stats()

@@ -198,3 +198,23 @@ def serving_workload(seed: int, n_requests: int, page_rate: float, n_pages_ws: i
                 seen.add(v)
                 seg[i] = v
     return arrival, ops, offsets, pages
+
+
+def window_trace(seed: int, n_pages: int, length: int, hot_frac: float = 0.6, zipf_s: float = 1.1) -> np.ndarray:
+    """Page-access trace of one synthetic client, for the sliding-window driver.
+
+    Each access is, with probability ``hot_frac``, a Zipf(zipf_s)-ranked page
+    of a seeded permutation of the client's pages (a hot set) and otherwise
+    the next page of a sequential scan that wraps around (streaming access).
+    Page numbers are relative to the client's first page.
+    """
+    u = uniform01(seed, 0, length)
+    k = np.arange(1, n_pages + 1, dtype=np.float64)
+    cdf = np.cumsum(k ** -zipf_s)
+    cdf /= cdf[-1]
+    rank = np.searchsorted(cdf, uniform01(seed ^ 0x7777, 0, length), side="right").clip(0, n_pages - 1)
+    perm = (splitmix64(seed ^ 0x9999, 0, n_pages)).argsort()
+    hot = u < hot_frac
+    start = int(splitmix64(seed ^ 0x5555, 0, 1)[0] % np.uint64(n_pages))
+    scan = (start + np.cumsum(~hot) - 1) % n_pages
+    return np.where(hot, perm[rank], scan).astype(np.uint64)

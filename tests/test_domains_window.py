@@ -1,0 +1,105 @@
+"""Per-page domains (the paper's client PID in the nonce) and the
+sliding-window client driver (the fault / eviction stream of Sec. 4.3),
+checked against the oracle on the GPU."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import PAGE
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ms():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2004_09252_b300 import memshield
+    return memshield
+
+
+def oracle_by_domain(key, plain, slots, ids, domains):
+    out = plain.copy()
+    for dom in np.unique(domains):
+        sel = domains == dom
+        oracle.crypt_pages(key, out, slots[sel], ids[sel], domain=int(dom))
+    return out
+
+
+@pytest.mark.parametrize("shape", [None, (1, 256, 10, 1, 0), (4, 128, 10, 1, 0), (2, 512, 10, 0, 1)])
+def test_per_page_domains_host_and_device_lists(ms, key1, shape):
+    n_slots, n = 300, 257
+    plain = synth.page_bytes(90, 0, n_slots)
+    slots = synth.scattered_slots(91, n_slots, n).astype(np.uint64)
+    ids = synth.splitmix64(92, 0, n).astype(np.uint64)
+    doms = (synth.splitmix64(93, 0, n) % np.uint64(5)).astype(np.uint32) * np.uint32(0x1234567)
+    want = oracle_by_domain(key1, plain, slots, ids, doms)
+    with ms.Context(key1, stream=torch.cuda.current_stream(), domain=999) as ctx:
+        if shape:
+            ctx.set_shape(*shape)
+        d = torch.from_numpy(plain).cuda()
+        ctx.crypt_pages_dom(ms.pages_dom_array(d.data_ptr() + PAGE * slots, ids, doms))
+        ctx.sync_checked()
+        assert np.array_equal(d.cpu().numpy(), want)
+        d2 = torch.from_numpy(plain).cuda()
+        lst = torch.from_numpy(ms.pages_dom_array(d2.data_ptr() + PAGE * slots, ids, doms).view(np.uint8)).cuda()
+        ctx.crypt_pages_dom_dev(lst, n)
+        ctx.sync_checked()
+        assert np.array_equal(d2.cpu().numpy(), want)
+
+
+def test_server_requests_with_domains(ms, key1):
+    n = 512
+    plain = synth.page_bytes(94, 0, n)
+    h = torch.from_numpy(plain.copy()).pin_memory()
+    pages = synth.scattered_slots(95, n, 400)
+    doms = np.repeat(np.array([7, 11, 13, 7], dtype=np.uint32), 100)
+    with ms.Context(key1, domain=5) as ctx, ms.Server(ctx, h, n) as srv:
+        ts = [srv.submit(ms.MS_ENCRYPT, pages[i:i + 4], domain=int(doms[i])) for i in range(0, 400, 4)]
+        for t in ts:
+            srv.wait(t)
+    want = oracle_by_domain(key1, plain, pages.astype(np.uint64), pages.astype(np.uint64), doms)
+    assert np.array_equal(h.numpy(), want)
+
+
+@pytest.mark.parametrize("window,batch", [(4, 1), (8, 1), (8, 4), (16, 9)])
+def test_sliding_window_clients(ms, key1, window, batch):
+    """Three clients with their own PIDs fault through FIFO windows; afterwards
+    exactly their final-window pages are in clear, the rest encrypted."""
+    per, n_clients = 128, 3
+    n = per * n_clients
+    plain = synth.page_bytes_fast(96, 0, n)
+    h = torch.from_numpy(plain.copy()).pin_memory()
+    doms = [1001, 2002, 3003]
+    clients = [(doms[c], c * per, per, synth.window_trace(97 + c, per, 1500)) for c in range(n_clients)]
+    with ms.Context(key1) as ctx, ms.Server(ctx, h, n) as srv:
+        for c in range(n_clients):             # every client page starts encrypted
+            srv.wait(srv.submit(ms.MS_ENCRYPT, np.arange(c * per, (c + 1) * per), domain=doms[c]))
+        stats, wins = srv.run_window_clients(window, batch, clients)
+    ws = h.numpy()
+    for c in range(n_clients):
+        st, win = stats[c], wins[c]
+        assert st["accesses"] == 1500 and st["hits"] + st["faults"] == 1500
+        assert st["faults"] - st["evictions"] == len(win) == st["final_window_pages"] <= window
+        assert len(set(win)) == len(win) and all(c * per <= p < (c + 1) * per for p in win)
+        enc = np.array(sorted(set(range(c * per, (c + 1) * per)) - set(win)), dtype=np.uint64)
+        want = plain[c * per * PAGE:(c + 1) * per * PAGE].copy()
+        rel = enc - np.uint64(c * per)
+        oracle.crypt_pages(key1, want, rel, enc, domain=doms[c])
+        assert np.array_equal(ws[c * per * PAGE:(c + 1) * per * PAGE], want), f"client {c}"
+        assert st["fault_p50_us"] > 0 and st["fault_p99_us"] >= st["fault_p50_us"]
+
+
+def test_window_rejects_bad_configs(ms, key1):
+    n = 64
+    h = torch.zeros(n * PAGE, dtype=torch.uint8).pin_memory()
+    with ms.Context(key1) as ctx, ms.Server(ctx, h, n) as srv:
+        tr = np.zeros(4, dtype=np.uint64)
+        with pytest.raises(ms.MemShieldError):
+            srv.run_window_clients(0, 1, [(1, 0, 32, tr)])          # empty window
+        with pytest.raises(ms.MemShieldError):
+            srv.run_window_clients(4, 1, [(1, 0, 32, tr), (2, 16, 32, tr)])   # overlapping clients
+        with pytest.raises(ms.MemShieldError):
+            srv.run_window_clients(4, 1, [(1, 0, 32, np.array([40], dtype=np.uint64))])  # outside the client
