@@ -387,6 +387,9 @@ void ms_server::fail_all(int code) {
     slot(t).state.store(kDone);
   }
   incoming.clear();
+  {
+    std::lock_guard<std::mutex> lk2(done_mu);
+  }
   done_cv.notify_all();
 }
 
@@ -617,17 +620,21 @@ int ms_server_poll(ms_server *s, uint64_t ticket) {
 int ms_server_wait(ms_server *s, uint64_t ticket, uint32_t timeout_ms) {
   if (!s) return MS_EINVAL;
   const auto deadline = clk::now() + std::chrono::milliseconds(timeout_ms);
-  for (;;) {
-    int p = ms_server_poll(s, ticket);
-    if (p < 0) return p;
-    if (p == 1) return MS_OK;
-    std::unique_lock<std::mutex> lk(s->done_mu);
-    if (s->done_cv.wait_until(lk, deadline) == std::cv_status::timeout) {
-      p = ms_server_poll(s, ticket);
-      if (p < 0) return p;
-      return p == 1 ? MS_OK : MS_ETIMEDOUT;
-    }
+  // poll for ~50 us first: most waits end within a wave's round trip
+  const auto spin_end = clk::now() + std::chrono::microseconds(50);
+  int p = ms_server_poll(s, ticket);
+  while (p == 0 && clk::now() < spin_end && clk::now() < deadline) {
+    nap_ns(1000);
+    p = ms_server_poll(s, ticket);
   }
+  if (p == 0) {
+    // the completing thread stores the state, then takes done_mu and notifies:
+    // checking the state under done_mu cannot miss that notification
+    std::unique_lock<std::mutex> lk(s->done_mu);
+    s->done_cv.wait_until(lk, deadline, [&] { return (p = ms_server_poll(s, ticket)) != 0; });
+  }
+  if (p < 0) return p;
+  return p == 1 ? MS_OK : MS_ETIMEDOUT;
 }
 
 int ms_server_replay(ms_server *s, size_t n, const double *arrival_s, const int *ops, const uint32_t *domains,
