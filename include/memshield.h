@@ -429,6 +429,63 @@ int ms_window_run(ms_server *srv, const ms_window_config *cfg, const ms_window_c
 int ms_server_destroy(ms_server *srv);
 
 /*
+ * ---- Resident workers (the paper's always-running GPU module, bounded) ----
+ *
+ * Sec. 4.4: the GPU module is a kernel that keeps running; each of its
+ * workers (a CUDA block) takes pages from its own queue in host/device
+ * mapped memory, filled by many host threads.  Here each worker is a
+ * one-CTA kernel on its own stream polling its own ring in pinned, mapped
+ * host memory; a request is one page (the fault path) whose bytes may live in
+ * device memory or in pinned host memory (then the worker reads and writes
+ * them over the host link: no copies, no launch per request).
+ *
+ * Bounds (no wait is unbounded): a worker leaves after idle_exit_us without
+ * work, after max_run_ms in total, or at ms_resident_destroy; a submit or a
+ * wait that finds it gone launches it again.  Requests are assigned to
+ * workers round-robin; one worker serves its requests in order.  A page must
+ * not be in flight twice.  ChaCha20 contexts only (cfg.rounds = 20).
+ */
+typedef struct ms_resident ms_resident;
+
+typedef struct ms_resident_config {
+  uint32_t workers;       /* worker CTAs, 1..64 (default 4) */
+  uint32_t ring_entries;  /* requests per worker ring, a power of two, 4..2^20 (default 4096) */
+  uint32_t idle_exit_us;  /* a worker leaves after this long without work (default 200000) */
+  uint32_t max_run_ms;    /* and after this long in total, 1..600000 (default 10000) */
+} ms_resident_config;
+
+typedef struct ms_resident_stats {
+  uint64_t requests;         /* submitted */
+  uint64_t launches;         /* worker launches (first start and every restart) */
+  uint64_t max_run_exits;    /* launches that ended by max_run_ms */
+  uint64_t workers_running;  /* workers currently running */
+} ms_resident_stats;
+
+void ms_resident_config_default(ms_resident_config *cfg);
+/* Allocates the rings (32 B per entry) and done words in pinned mapped memory. */
+int ms_resident_create(ms_ctx *ctx, const ms_resident_config *cfg, ms_resident **out);
+/* Queue one page; *ticket identifies it.  MS_EBUSY: the worker's ring is full. */
+int ms_resident_submit(ms_resident *res, const ms_page_dom *page, uint64_t *ticket);
+/* 1 = done (the page is written back), 0 = pending, < 0 = error. */
+int ms_resident_poll(ms_resident *res, uint64_t ticket);
+int ms_resident_wait(ms_resident *res, uint64_t ticket, uint32_t timeout_ms);
+int ms_resident_get_stats(const ms_resident *res, ms_resident_stats *out);
+/* Stop the workers (bounded wait) and free.  NULL is a no-op. */
+int ms_resident_destroy(ms_resident *res);
+/*
+ * Open-loop replay over a pinned, mapped host working set of n_pages pages at
+ * host_base (page index i = page id i): request r (domain domains[r], or the
+ * context's when NULL) on page_index[offsets[r] .. offsets[r + 1]) is
+ * submitted at arrival_s[r], one resident request per page, and completes
+ * when all its pages are done; a page still in flight from an earlier
+ * request is waited for first.  latency_s[r] counts from the scheduled
+ * arrival.  The working set is read and written in place over the host link.
+ */
+int ms_resident_replay(ms_resident *res, void *host_base, uint64_t n_pages, size_t n_requests,
+                       const double *arrival_s, const uint32_t *domains, const uint64_t *offsets,
+                       const uint64_t *page_index, double *latency_s, double *makespan_s, uint32_t timeout_ms);
+
+/*
  * Allocation-free variant of ms_encrypt_pages / ms_decrypt_pages.  The paper
  * has no counterpart: this is a library convenience.
  *

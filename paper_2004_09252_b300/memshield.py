@@ -126,6 +126,15 @@ class ms_window_stats(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("fault_p50_us", "fault_p99_us", "fault_max_us", "elapsed_s")]
 
 
+class ms_resident_config(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_uint32), ("ring_entries", ctypes.c_uint32), ("idle_exit_us", ctypes.c_uint32),
+                ("max_run_ms", ctypes.c_uint32)]
+
+
+class ms_resident_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("requests", "launches", "max_run_exits", "workers_running")]
+
+
 def _load():
     path = _build.LIB
     if not os.path.exists(path):
@@ -169,6 +178,14 @@ def _load():
         "ms_server_replay": (I, [P, S, P, P, P, P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.c_uint32]),
         "ms_server_submit_dom": (I, [P, I, ctypes.c_uint32, P, ctypes.c_uint32, ctypes.POINTER(U64)]),
         "ms_crypt_pages_dom": (I, [P, P, S]),
+        "ms_resident_config_default": (None, [ctypes.POINTER(ms_resident_config)]),
+        "ms_resident_create": (I, [P, ctypes.POINTER(ms_resident_config), ctypes.POINTER(P)]),
+        "ms_resident_submit": (I, [P, P, ctypes.POINTER(U64)]),
+        "ms_resident_poll": (I, [P, U64]),
+        "ms_resident_wait": (I, [P, U64, ctypes.c_uint32]),
+        "ms_resident_get_stats": (I, [P, ctypes.POINTER(ms_resident_stats)]),
+        "ms_resident_destroy": (I, [P]),
+        "ms_resident_replay": (I, [P, P, U64, S, P, P, P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.c_uint32]),
         "ms_window_run": (I, [P, ctypes.POINTER(ms_window_config), ctypes.POINTER(ms_window_client), S,
                               ctypes.POINTER(ms_window_stats), P, ctypes.c_uint32]),
         "ms_crypt_pages_dom_dev": (I, [P, P, S]),
@@ -514,6 +531,74 @@ class Server:
     def destroy(self) -> int:
         if self.handle:
             rc = _lib.ms_server_destroy(self.handle)
+            self.handle = None
+            return rc
+        return MS_OK
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+
+class Resident:
+    """An ms_resident: worker kernels that keep running and take single pages from mapped rings."""
+
+    def __init__(self, ctx: Context, workers: int = 0, ring_entries: int = 0, idle_exit_us: int = 0,
+                 max_run_ms: int = 0):
+        cfg = ms_resident_config()
+        _lib.ms_resident_config_default(ctypes.byref(cfg))
+        if workers:
+            cfg.workers = workers
+        if ring_entries:
+            cfg.ring_entries = ring_entries
+        if idle_exit_us:
+            cfg.idle_exit_us = idle_exit_us
+        if max_run_ms:
+            cfg.max_run_ms = max_run_ms
+        h = ctypes.c_void_p()
+        _check(_lib.ms_resident_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "ms_resident_create")
+        self.handle = h.value
+        self.ctx = ctx
+
+    def submit(self, addr: int, page_id: int, domain: int = 0) -> int:
+        """Queue one page; returns its ticket, or -1 when the worker's ring is full."""
+        e = pages_dom_array([addr], [page_id], [domain])
+        t = ctypes.c_uint64()
+        rc = _lib.ms_resident_submit(self.handle, e.ctypes.data, ctypes.byref(t))
+        if rc == MS_EBUSY:
+            return -1
+        _check(rc, "ms_resident_submit")
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        return _lib.ms_resident_poll(self.handle, ticket)
+
+    def wait(self, ticket: int, timeout_ms: int = 10000) -> None:
+        _check(_lib.ms_resident_wait(self.handle, ticket, timeout_ms), "ms_resident_wait")
+
+    def stats(self) -> dict:
+        st = ms_resident_stats()
+        _check(_lib.ms_resident_get_stats(self.handle, ctypes.byref(st)), "ms_resident_get_stats")
+        return {f: getattr(st, f) for f, _ in ms_resident_stats._fields_}
+
+    def replay(self, host_base, n_pages: int, arrival_s, offsets, page_index, domains=None, timeout_ms: int = 60000):
+        arrival_s = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        page_index = np.ascontiguousarray(page_index, dtype=np.uint64)
+        dom = None if domains is None else np.ascontiguousarray(domains, dtype=np.uint32)
+        lat = np.empty(arrival_s.size, dtype=np.float64)
+        mk = ctypes.c_double()
+        _check(_lib.ms_resident_replay(self.handle, _ptr(host_base), n_pages, arrival_s.size, arrival_s.ctypes.data,
+                                       None if dom is None else dom.ctypes.data, offsets.ctypes.data,
+                                       page_index.ctypes.data, lat.ctypes.data, ctypes.byref(mk), timeout_ms),
+               "ms_resident_replay")
+        return lat, mk.value
+
+    def destroy(self) -> int:
+        if self.handle:
+            rc = _lib.ms_resident_destroy(self.handle)
             self.handle = None
             return rc
         return MS_OK
