@@ -605,11 +605,18 @@ def serve_rows(args, rates, modes, seconds):
         mode_ids = {"continuous": ms.MS_SERVE_CONTINUOUS, "one_per_launch": ms.MS_SERVE_ONE_PER_LAUNCH,
                     "zero_copy": ms.MS_SERVE_ZERO_COPY}
         for name in modes:
-            mode = mode_ids[name]
-            with ms.Server(ctx, ws, n, mode=mode, copy_threads=args.copy_threads,
-                           waves_in_flight=args.waves_in_flight, idle_spin_us=args.idle_spin_us) as srv:
-                lat, makespan = srv.replay(arrival, ops, offsets, pages, timeout_ms=600000)
-                st = srv.stats()
+            if name == "resident":
+                with ms.Resident(ctx, workers=args.resident_workers) as res:
+                    lat, makespan = res.replay(ws, n, arrival, offsets, pages, timeout_ms=60000)
+                    rst = res.stats()
+                st = {"waves": rst["requests"], "max_wave_requests": 1, "conflict_waits": 0, "budget_waits": 0,
+                      "gather_ns": 0, "scatter_ns": 0}
+            else:
+                mode = mode_ids[name]
+                with ms.Server(ctx, ws, n, mode=mode, copy_threads=args.copy_threads,
+                               waves_in_flight=args.waves_in_flight, idle_spin_us=args.idle_spin_us) as srv:
+                    lat, makespan = srv.replay(arrival, ops, offsets, pages, timeout_ms=600000)
+                    st = srv.stats()
             total = int(offsets[-1])
             us = lat * 1e6
             rows.append({"offered_pages_per_s": rate, "mode": name, "requests": n_req, "pages": total,
@@ -753,6 +760,7 @@ def main():
     ap.add_argument("--serve-rates", type=lambda v: [float(x) for x in v.split(",")], default=SERVE_RATES)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--copy-threads", type=int, default=8)
+    ap.add_argument("--resident-workers", type=int, default=8)
     ap.add_argument("--window-client-pages", type=int, default=16384)
     ap.add_argument("--window-trace", type=int, default=50000)
     ap.add_argument("--window-clients", type=lambda v: [int(x) for x in v.split(",")], default=[1, 2, 4])

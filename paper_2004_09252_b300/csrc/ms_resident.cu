@@ -17,6 +17,7 @@
 // state.  One of the two sees the other: either the worker stays
 // (RUNNING) or the host sees EXITED and launches the worker again on the
 // same stream, where the new launch starts after the old one has returned.
+#include <sys/prctl.h>
 #include <time.h>
 
 #include <algorithm>
@@ -158,7 +159,14 @@ __global__ void __launch_bounds__(kWorkerThreads) k_resident(const ResidentArgs 
   }
 }
 
+// Short naps must stay short: the first nap on a thread drops its timer
+// slack (default 50 us) to 1 us.
 inline void nap_ns(long ns) {
+  thread_local bool slack_set = false;
+  if (!slack_set) {
+    prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);
+    slack_set = true;
+  }
   struct timespec ts = {0, ns};
   nanosleep(&ts, nullptr);
 }
