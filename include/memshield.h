@@ -196,6 +196,21 @@ const char *ms_strerror(int code);
 int ms_last_cuda_error(const ms_ctx *ctx);
 
 /*
+ * Host-side fault injection, for tests of error handling (no GPU fault is
+ * ever caused).  Arms a one-shot failure: the (countdown + 1)-th call at a
+ * site in site_mask behaves as if the CUDA runtime had returned cuda_error
+ * there (the real call is skipped), so the entry point returns MS_ECUDA and
+ * ms_last_cuda_error gives cuda_error.  site_mask 0 disarms.  Process-wide.
+ */
+enum ms_fault_site {
+  MS_FAULT_LAUNCH = 1,  /* page-kernel launches (one-launch forms) */
+  MS_FAULT_COPY = 2,    /* host->device copies of entry lists and host-streamed chunks */
+  MS_FAULT_GRAPH = 4,   /* batched-form graph launches */
+  MS_FAULT_SERVER = 8   /* a served wave's first copy: the server fails its pending requests */
+};
+int ms_debug_inject_fault(int site_mask, int countdown, int cuda_error);
+
+/*
  * Host pages, streamed (end-to-end form).  n_pages pages back to back at the
  * HOST address host_base (pinned memory gives overlapped copies; pageable
  * memory works but serialises); page k has id first_page_id + k.  The range

@@ -212,7 +212,8 @@ int ms_batch_submit(ms_batch *b) {
       e = capture(b, q);
       if (e != cudaSuccess) return cuda_fail(c, e);
     }
-    e = cudaGraphLaunch(q.exec, c->stream);
+    e = injected(MS_FAULT_GRAPH);
+    if (e == cudaSuccess) e = cudaGraphLaunch(q.exec, c->stream);
     b->stats.graph_launches += 1;
   } else {
     QueueKernel k;

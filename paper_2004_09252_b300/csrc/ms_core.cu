@@ -4,6 +4,7 @@
 #include <time.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
@@ -18,6 +19,19 @@ namespace ms {
 int cuda_fail(ms_ctx *c, cudaError_t e) {
   if (c) c->last_cuda.store((int)e);
   return MS_ECUDA;
+}
+
+namespace {
+std::atomic<int> g_fault_mask{0};
+std::atomic<int> g_fault_countdown{0};
+std::atomic<int> g_fault_error{0};
+}  // namespace
+
+cudaError_t injected(int site) {
+  if (!(g_fault_mask.load(std::memory_order_relaxed) & site)) return cudaSuccess;
+  if (g_fault_countdown.fetch_sub(1) != 0) return cudaSuccess;
+  g_fault_mask.store(0);  // one shot
+  return (cudaError_t)g_fault_error.load();
 }
 
 // Bounded wait on an event: poll, spinning for the first 50 us and then
@@ -82,7 +96,8 @@ int submit_list_host(ms_ctx *c, const E *pages, size_t n) {
       if (rc != MS_OK) return rc;
     }
     std::memcpy(s.h, pages + off, cnt * sizeof(E));
-    cudaError_t e = cudaMemcpyAsync(s.d, s.h, cnt * sizeof(E), cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e = injected(MS_FAULT_COPY);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.d, s.h, cnt * sizeof(E), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     PageArgs a = make_args(c);
     set_list<E>(a, static_cast<const E *>(s.d));
@@ -142,6 +157,16 @@ const char *ms_strerror(int code) {
 }
 
 int ms_last_cuda_error(const ms_ctx *ctx) { return ctx ? ctx->last_cuda.load() : 0; }
+
+int ms_debug_inject_fault(int site_mask, int countdown, int cuda_error) {
+  if (site_mask & ~(MS_FAULT_LAUNCH | MS_FAULT_COPY | MS_FAULT_GRAPH | MS_FAULT_SERVER)) return MS_EINVAL;
+  if (countdown < 0 || (site_mask && cuda_error == 0)) return MS_EINVAL;
+  g_fault_mask.store(0);
+  g_fault_error.store(cuda_error);
+  g_fault_countdown.store(countdown);
+  g_fault_mask.store(site_mask);
+  return MS_OK;
+}
 
 static void release(ms_ctx *c) {
   for (auto &s : c->slots) {
@@ -418,7 +443,8 @@ int ms_crypt_host(ms_ctx *c, int op, void *host_base, uint64_t first_page_id, si
     const size_t np = std::min(pages_per_chunk, n_pages - p0);
     const size_t bytes = np * MS_PAGE_BYTES;
     cudaStream_t s = c->hs[si];
-    e = cudaMemcpyAsync(c->hs_buf[si], hb + p0 * MS_PAGE_BYTES, bytes, cudaMemcpyHostToDevice, s);
+    e = injected(MS_FAULT_COPY);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->hs_buf[si], hb + p0 * MS_PAGE_BYTES, bytes, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(c, e);
     PageArgs a = make_args(c);
     a.base = (uint8_t *)c->hs_buf[si];

@@ -90,6 +90,10 @@ class DeviceGuard {
 };
 
 int cuda_fail(ms_ctx *c, cudaError_t e);
+
+// Host-side fault injection (tests): returns the injected error when the
+// armed countdown reaches zero at a site in the armed mask, else cudaSuccess.
+cudaError_t injected(int site);
 int wait_event(ms_ctx *c, cudaEvent_t ev, uint32_t timeout_ms);
 PageArgs make_args(const ms_ctx *c);
 // Launch K1 with the context's tuned shape (list mode when a.pages != nullptr).

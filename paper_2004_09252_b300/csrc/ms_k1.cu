@@ -77,6 +77,8 @@ cudaError_t launch_pages_shape(const PageArgs &a, int rounds, const Tune &t, boo
   if (!e) return cudaErrorInvalidValue;
   if (a.n_pages == 0) return cudaSuccess;
   const int mode = range ? kModeRange : (a.dpages ? kModeListDom : kModeList);
+  const cudaError_t f = injected(MS_FAULT_LAUNCH);
+  if (f != cudaSuccess) return f;
   return e->fn[mode](a, t.tpc, s);
 }
 

@@ -309,8 +309,8 @@ int ms_server::issue(Wave &w) {
   st_gather_ns.fetch_add(now_ns() - tg);
   const size_t off = (size_t)w.pos * MS_PAGE_BYTES, bytes = (size_t)w.len * MS_PAGE_BYTES;
   cudaStream_t sw = s_work[wave_seq++ & 1];
-  cudaError_t e = cudaSuccess;
-  if (!zc) e = cudaMemcpyAsync(d_stage + off, h_stage + off, bytes, cudaMemcpyHostToDevice, s_in);
+  cudaError_t e = injected(MS_FAULT_SERVER);
+  if (e == cudaSuccess && !zc) e = cudaMemcpyAsync(d_stage + off, h_stage + off, bytes, cudaMemcpyHostToDevice, s_in);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_ent + w.pos, h_ent + w.pos, sizeof(ms_page_dom) * w.len, cudaMemcpyHostToDevice, s_in);
   if (e == cudaSuccess) e = cudaEventRecord(w.ev_h2d, s_in);

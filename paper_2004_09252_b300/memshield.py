@@ -21,6 +21,7 @@ MS_KEY_BYTES = 32
 MS_OK, MS_EINVAL, MS_ENOTINIT, MS_ENOMEM, MS_ECUDA, MS_ETIMEDOUT, MS_EBUSY, MS_ERANGE = 0, -1, -2, -3, -4, -5, -6, -7
 MS_ENCRYPT, MS_DECRYPT = 0, 1
 MS_NOALLOC_MAX_PAGES = 16384
+MS_FAULT_LAUNCH, MS_FAULT_COPY, MS_FAULT_GRAPH, MS_FAULT_SERVER = 1, 2, 4, 8
 
 PAGE_DTYPE = np.dtype([("addr", "<u8"), ("page_id", "<u8")])
 PAGE_DOM_DTYPE = np.dtype([("addr", "<u8"), ("page_id", "<u8"), ("domain", "<u4"), ("reserved0", "<u4"),
@@ -158,6 +159,7 @@ def _load():
         "ms_shutdown": (I, [P]),
         "ms_strerror": (ctypes.c_char_p, [I]),
         "ms_last_cuda_error": (I, [P]),
+        "ms_debug_inject_fault": (I, [I, I, I]),
         "ms_crypt_host": (I, [P, I, P, U64, S, S, I]),
         "ms_get_shape": (I, [P, ctypes.POINTER(ms_shape)]),
         "ms_set_shape": (I, [P, ctypes.POINTER(ms_shape)]),
@@ -213,6 +215,11 @@ def _check(code: int, where: str) -> int:
     if code != MS_OK:
         raise MemShieldError(code, where)
     return code
+
+
+def inject_fault(site_mask: int, countdown: int = 0, cuda_error: int = 719) -> None:
+    """Arm a one-shot host-side failure (719 = cudaErrorLaunchFailure by default)."""
+    _check(_lib.ms_debug_inject_fault(site_mask, countdown, cuda_error), "ms_debug_inject_fault")
 
 
 def config_default() -> ms_config:
