@@ -483,6 +483,8 @@ int ms_resident_create(ms_ctx *ctx, const ms_resident_config *cfg, ms_resident *
 int ms_resident_submit(ms_resident *res, const ms_page_dom *page, uint64_t *ticket);
 /* 1 = done (the page is written back), 0 = pending, < 0 = error. */
 int ms_resident_poll(ms_resident *res, uint64_t ticket);
+/* Polls with 0.5 us naps; the calling thread's timer slack is set to 1 us on
+ * its first nap so that they stay short. */
 int ms_resident_wait(ms_resident *res, uint64_t ticket, uint32_t timeout_ms);
 int ms_resident_get_stats(const ms_resident *res, ms_resident_stats *out);
 /* Stop the workers (bounded wait) and free.  NULL is a no-op. */
