@@ -438,6 +438,7 @@ int ms_crypt_host(ms_ctx *c, int op, void *host_base, uint64_t first_page_id, si
   const size_t pages_per_chunk = chunk_bytes / MS_PAGE_BYTES;
   uint8_t *hb = (uint8_t *)host_base;
   size_t chunk = 0;
+  int fail = MS_OK;  // the first error; chunks already issued are still drained
   for (size_t p0 = 0; p0 < n_pages; p0 += pages_per_chunk, ++chunk) {
     const int si = (int)(chunk % n_streams);
     const size_t np = std::min(pages_per_chunk, n_pages - p0);
@@ -445,29 +446,34 @@ int ms_crypt_host(ms_ctx *c, int op, void *host_base, uint64_t first_page_id, si
     cudaStream_t s = c->hs[si];
     e = injected(MS_FAULT_COPY);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->hs_buf[si], hb + p0 * MS_PAGE_BYTES, bytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(c, e);
-    PageArgs a = make_args(c);
-    a.base = (uint8_t *)c->hs_buf[si];
-    a.first_id = first_page_id + p0;
-    a.n_pages = np;
-    e = launch_pages(c, a, s);
-    if (e != cudaSuccess) return cuda_fail(c, e);
-    e = cudaMemcpyAsync(hb + p0 * MS_PAGE_BYTES, c->hs_buf[si], bytes, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(c, e);
+    if (e == cudaSuccess) {
+      PageArgs a = make_args(c);
+      a.base = (uint8_t *)c->hs_buf[si];
+      a.first_id = first_page_id + p0;
+      a.n_pages = np;
+      e = launch_pages(c, a, s);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hb + p0 * MS_PAGE_BYTES, c->hs_buf[si], bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) {
+      fail = cuda_fail(c, e);
+      ++chunk;
+      break;
+    }
   }
+  // Wait (bounded: timeout_ms per chunk) for everything issued, also after an
+  // error, so no copy lands in the caller's buffer after this call returns.
   const uint64_t n_chunks = chunk;
   int rc = MS_OK;
-  for (int i = 0; i < n_streams && (uint64_t)i < n_chunks; ++i) {
-    e = cudaEventRecord(c->hs_ev[i], c->hs[i]);
-    if (e != cudaSuccess) return cuda_fail(c, e);
-  }
-  // bound: timeout_ms per chunk
+  const int used = (int)std::min<uint64_t>((uint64_t)n_streams, n_chunks);
   const uint64_t limit = (uint64_t)c->cfg.timeout_ms * std::max<uint64_t>(1, n_chunks);
-  for (int i = 0; i < n_streams && (uint64_t)i < n_chunks; ++i) {
-    int r = wait_event(c, c->hs_ev[i], (uint32_t)std::min<uint64_t>(limit, 0xffffffffu));
+  for (int i = 0; i < used; ++i) {
+    e = cudaEventRecord(c->hs_ev[i], c->hs[i]);
+    int r = (e == cudaSuccess) ? wait_event(c, c->hs_ev[i], (uint32_t)std::min<uint64_t>(limit, 0xffffffffu))
+                               : cuda_fail(c, e);
     if (r != MS_OK && rc == MS_OK) rc = r;
   }
-  return rc;
+  return fail != MS_OK ? fail : rc;
 }
 
 }  // extern "C"
