@@ -1,0 +1,62 @@
+"""Parity at the full sizes of the host-streaming (4 GiB pinned host buffer)
+and serving (16 GiB pinned working set) configurations, in the launch
+configurations the benchmark uses; sampled pages against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import PAGE, sample_pages
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def ms():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2004_09252_b300 import memshield
+    return memshield
+
+
+def test_host_config_4gib(ms, key1):
+    """1,048,576 pages of seed 4 streamed in 16 MiB chunks on 2 streams."""
+    n = 1048576
+    h = torch.empty(n * PAGE, dtype=torch.uint8).pin_memory()
+    synth.fill_pages(h.data_ptr(), 4, 0, n)
+    with ms.Context(key1) as ctx:
+        ctx.crypt_host(ms.MS_ENCRYPT, h, 0, n, 16 << 20, 2)
+        hv = h.numpy().reshape(n, PAGE)
+        for p in sample_pages(130, n, 48):
+            pg = synth.page_bytes(4, int(p), 1)
+            oracle.page_xor(key1, int(p), pg)
+            assert np.array_equal(hv[p], pg), f"page {p}"
+        ctx.crypt_host(ms.MS_DECRYPT, h, 0, n, 16 << 20, 2)
+    for p in sample_pages(131, n, 48):
+        assert np.array_equal(hv[p], synth.page_bytes(4, int(p), 1))
+
+
+def test_serving_config_16gib(ms, key1):
+    """One second of the serving mix at 141k pages/s over the 16 GiB working
+    set (seed 5), continuous batching: every touched page ends as the closed
+    form says (odd number of applications = encrypted)."""
+    n = 4194304
+    ws = torch.empty(n * PAGE, dtype=torch.uint8).pin_memory()
+    synth.fill_pages(ws.data_ptr(), 5, 0, n)
+    arrival, ops, offsets, pages = synth.serving_workload(5, 17625, 1.41e5, n)
+    with ms.Context(key1) as ctx, ms.Server(ctx, ws, n) as srv:
+        lat, makespan = srv.replay(arrival, ops, offsets, pages)
+    assert (lat >= 0).all()
+    counts = np.bincount(pages.astype(np.int64), minlength=n)
+    touched = np.nonzero(counts)[0]
+    pick = touched[(synth.splitmix64(132, 0, 64) % np.uint64(len(touched))).astype(np.int64)]
+    wv = ws.numpy().reshape(n, PAGE)
+    for p in pick:
+        pg = synth.page_bytes(5, int(p), 1)
+        if counts[p] % 2:
+            oracle.page_xor(key1, int(p), pg)
+        assert np.array_equal(wv[p], pg), f"page {p}"
+    untouched = np.setdiff1d(np.arange(0, n, 65537), touched)
+    for p in untouched[:16]:
+        assert np.array_equal(wv[p], synth.page_bytes(5, int(p), 1))
