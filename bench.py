@@ -391,8 +391,8 @@ def run_batching(args):
     import synth
     from paper_2004_09252_b300 import memshield as ms
 
-    n_slots = 2097152
-    sizes, slots, ops = synth.batching_workload(3)
+    n_slots = int(2097152 * args.batching_scale)
+    sizes, slots, ops = synth.batching_workload(3, n_requests=int(20000 * args.batching_scale), n_slots=n_slots)
     n_req, total = len(sizes), int(sizes.sum())
     key = synth.key_bytes(1)
     a = torch.empty(n_slots * PAGE, dtype=torch.uint8, device="cuda")
@@ -401,7 +401,7 @@ def run_batching(args):
     b = a.clone()
     stream = torch.cuda.current_stream()
     ctx = ms.Context(key, stream=stream)
-    tune = ctx.autotune(65536)
+    tune = None if args.no_autotune else ctx.autotune(65536)
     offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
     sl = slots.astype(np.uint64)
     table_a = ms.pages_array(a.data_ptr() + PAGE * sl, sl)
@@ -458,9 +458,11 @@ def run_batching(args):
     print(json.dumps({
         "metric": "batching pages/s (persistent kernel + device queue + CUDA graph, autotuned)",
         "value": best["pages_per_s"], "unit": "pages/s", "higher_is_better": True,
-        "config": {"workload": "batching: 20,000 requests, Zipf(1.2) sizes 1..512 (mean 44.08), "
-                               f"{total} pages scattered without replacement over an 8 GiB buffer (2,097,152 "
-                               "slots), seed 3, ops 50/50 enc/dec", "pages": total, "requests": n_req},
+        "config": {"workload": (f"batching: {n_req} requests, Zipf(1.2) sizes 1..512 (mean 44.08), {total} pages "
+                                f"scattered without replacement over a {n_slots * PAGE / 2**30:g} GiB buffer "
+                                f"({n_slots} slots), seed 3, ops 50/50 enc/dec"
+                                + ("" if args.batching_scale == 1.0 else " (profiling case)")),
+                   "pages": total, "requests": n_req},
         "one_launch_per_request": {"wall_s": round(t_single, 5), "pages_per_s": round(total / t_single, 1),
                                    "gb_per_s": round(total * PAGE / t_single / 1e9, 2), "launches": n_req},
         "speedup_vs_one_launch_per_request": round(best["pages_per_s"] / (total / t_single), 2),
@@ -761,6 +763,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--copy-threads", type=int, default=8)
     ap.add_argument("--resident-workers", type=int, default=8)
+    ap.add_argument("--batching-scale", type=float, default=1.0, help="fraction of the batching workload (profiling)")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--window-client-pages", type=int, default=16384)
     ap.add_argument("--window-trace", type=int, default=50000)
     ap.add_argument("--window-clients", type=lambda v: [int(x) for x in v.split(",")], default=[1, 2, 4])
