@@ -50,7 +50,9 @@ static void store_le32(uint8_t *p, uint32_t v) {
   p[3] = (uint8_t)(v >> 24);
 }
 
-/* The ChaCha quarter round on four words of the state. */
+/* The ChaCha quarter round on four words of the state (Bernstein's ChaCha,
+ * the cipher Sec. 4.4 names; RFC 8439 Sec. 2.1): add, xor, rotate by 16, 12,
+ * 8 and 7. */
 void oracle_quarter_round(uint32_t *a, uint32_t *b, uint32_t *c, uint32_t *d) {
   *a += *b; *d ^= *a; *d = rotl32(*d, 16);
   *c += *d; *b ^= *c; *b = rotl32(*b, 12);
@@ -58,7 +60,8 @@ void oracle_quarter_round(uint32_t *a, uint32_t *b, uint32_t *c, uint32_t *d) {
   *c += *d; *b ^= *c; *b = rotl32(*b, 7);
 }
 
-/* The ChaCha permutation: rounds/2 double rounds, no feed-forward. */
+/* The ChaCha permutation: rounds/2 double rounds, each four column quarter
+ * rounds then four diagonal ones (RFC 8439 Sec. 2.3); no feed-forward. */
 void oracle_permute(uint32_t x[16], int rounds) {
   for (int r = 0; r < rounds; r += 2) {
     /* column round */
@@ -74,7 +77,9 @@ void oracle_permute(uint32_t x[16], int rounds) {
   }
 }
 
-/* One 64-byte keystream block: permute the input state, add it back, serialise LE. */
+/* One 64-byte keystream block (Sec. 4.4: 512 bits from the 256-bit key and a
+ * 128-bit value; RFC 8439 Sec. 2.3 layout): permute the input state, add it
+ * back, serialise little-endian. */
 void oracle_block(const uint8_t key[32], uint32_t counter, const uint8_t nonce[12], int rounds,
                   uint8_t out[64]) {
   static const char sigma[17] = "expand 32-byte k";
@@ -88,14 +93,18 @@ void oracle_block(const uint8_t key[32], uint32_t counter, const uint8_t nonce[1
   for (int i = 0; i < 16; i++) store_le32(out + 4 * i, x[i] + in[i]);
 }
 
-/* The per-page 96-bit nonce: page id (64 bits, LE) then the domain word (PID slot). */
+/* The per-page 96-bit nonce (Sec. 4.4: page address + client PID; the field
+ * order is this library's reading): page id (64 bits, LE) then the domain
+ * word (PID slot). */
 void oracle_page_nonce(uint64_t page_id, uint32_t domain, uint8_t nonce[12]) {
   store_le32(nonce + 0, (uint32_t)(page_id & 0xffffffffu));
   store_le32(nonce + 4, (uint32_t)(page_id >> 32));
   store_le32(nonce + 8, domain);
 }
 
-/* XOR one 4096-byte page with its 64 keystream blocks, counters 0..63. */
+/* XOR one 4096-byte page with its 64 keystream blocks, counters 0..63
+ * (Sec. 4.4: the counter is the index of the 512-bit block in the page, and
+ * the same XOR encrypts and decrypts). */
 void oracle_page_xor(const uint8_t key[32], uint64_t page_id, uint32_t domain, int rounds,
                      uint8_t *page) {
   uint8_t nonce[12], ks[ORACLE_BLOCK_BYTES];

@@ -246,3 +246,15 @@ def test_launches_follow_the_callers_stream(ms, key1):
         ctx.sync_checked()
         assert torch.equal(snap, d)
         assert not torch.equal(snap[:PAGE], torch.from_numpy(plain[:PAGE]).cuda())
+
+
+def test_launch_size_beyond_grid_limit_is_rejected_before_launch(ms, key1):
+    """A page count whose grid exceeds the launch limit is refused on the host
+    (MS_ECUDA, invalid configuration) and nothing is launched."""
+    d = torch.zeros(PAGE, dtype=torch.uint8, device="cuda")
+    with make_ctx(ms, key1) as ctx:
+        with pytest.raises(ms.MemShieldError) as e:
+            ctx.crypt_range(ms.MS_ENCRYPT, d, 0, 1 << 40)   # 2^40 pages: grid far above 2^31 - 1
+        assert e.value.code == ms.MS_ECUDA and ctx.last_cuda_error() == 9   # cudaErrorInvalidConfiguration
+        ctx.sync_checked()
+        assert int(d.sum()) == 0
