@@ -155,6 +155,8 @@ int ms_sync_for(ms_ctx *ctx, uint32_t timeout_ms);
 /*
  * Finish outstanding work (bounded), overwrite the device key with zeros and
  * free every resource.  ctx must not be used afterwards.  NULL is a no-op.
+ * MS_EBUSY (and nothing is freed) while a batch, server or resident worker
+ * set created on the context has not been destroyed.
  */
 int ms_shutdown(ms_ctx *ctx);
 

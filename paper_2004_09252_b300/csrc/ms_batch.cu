@@ -151,6 +151,7 @@ int ms_batch_create(ms_ctx *c, const ms_batch_config *cfg_in, ms_batch **out) {
     }
     std::memset(q.h, 0, kHeader);
   }
+  c->children.fetch_add(1);
   *out = b;
   return MS_OK;
 }
@@ -239,8 +240,11 @@ int ms_batch_get_stats(const ms_batch *b, ms_batch_stats *out) {
 
 int ms_batch_destroy(ms_batch *b) {
   if (!b) return MS_OK;
-  DeviceGuard g(b->ctx->device);
-  return free_batch(b);
+  ms_ctx *c = b->ctx;
+  DeviceGuard g(c->device);
+  const int rc = free_batch(b);
+  c->children.fetch_sub(1);
+  return rc;
 }
 
 }  // extern "C"

@@ -346,6 +346,7 @@ int ms_sync_for(ms_ctx *c, uint32_t timeout_ms) {
 
 int ms_shutdown(ms_ctx *c) {
   if (!c) return MS_OK;
+  if (c->children.load() > 0) return MS_EBUSY;  // a batch, server or resident set still uses it
   int rc = MS_OK;
   {
     DeviceGuard g(c->device);

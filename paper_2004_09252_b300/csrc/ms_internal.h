@@ -68,6 +68,7 @@ struct ms_ctx {
   size_t hs_cap = 0;
   std::mutex mu;
   std::atomic<int> last_cuda{0};
+  std::atomic<int> children{0};  // live batches, servers and resident worker sets on this context
   bool alive = false;
 };
 

@@ -296,6 +296,7 @@ int ms_resident_create(ms_ctx *c, const ms_resident_config *cfg_in, ms_resident 
     std::memset(w->h_sh, 0, sizeof(WorkerShared));
     w->h_sh->state = kExited;
   }
+  c->children.fetch_add(1);
   *out = r;
   return MS_OK;
 }
@@ -382,7 +383,9 @@ int ms_resident_destroy(ms_resident *r) {
     cudaEventDestroy(ev);
     if (r2 != MS_OK) return r2;  // a worker still runs: keep its memory allocated
   }
+  ms_ctx *c = r->ctx;
   free_resident(r);
+  c->children.fetch_sub(1);
   return rc;
 }
 

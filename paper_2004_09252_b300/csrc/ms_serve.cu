@@ -555,6 +555,7 @@ int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_serv
     free_server(s);
     return MS_ENOMEM;
   }
+  c->children.fetch_add(1);
   *out = s;
   return MS_OK;
 }
@@ -720,7 +721,9 @@ int ms_server_destroy(ms_server *s) {
     int r = wait_event(s->ctx, w.ev_done, s->ctx->cfg.timeout_ms);
     if (r != MS_OK) return r;  // still running on the GPU: leave the buffers allocated
   }
+  ms_ctx *c = s->ctx;
   free_server(s);
+  c->children.fetch_sub(1);
   return rc == MS_ETIMEDOUT ? MS_ETIMEDOUT : (rc ? rc : MS_OK);
 }
 

@@ -194,3 +194,16 @@ def test_batching_config_full_size(ms, key1):
         import oracle
         oracle.page_xor(key1, int(s), pg)
         assert np.array_equal(got[k], pg)
+
+
+def test_shutdown_refused_while_children_live(ms, key1):
+    ctx = ms.Context(key1)
+    b = ctx.batch(capacity=16)
+    h = torch.zeros(16 * PAGE, dtype=torch.uint8).pin_memory()
+    srv = ms.Server(ctx, h, 16)
+    assert ms.lib.ms_shutdown(ctx.handle) == ms.MS_EBUSY      # the context stays usable
+    b.destroy()
+    assert ms.lib.ms_shutdown(ctx.handle) == ms.MS_EBUSY
+    srv.wait(srv.submit(ms.MS_ENCRYPT, [1]))
+    srv.destroy()
+    assert ctx.shutdown() == ms.MS_OK
