@@ -366,9 +366,11 @@ class Context:
         return _lib.ms_last_cuda_error(self.handle)
 
     def shutdown(self) -> int:
+        """ms_shutdown; the handle stays valid when it returns MS_EBUSY (children alive)."""
         if self.handle:
             rc = _lib.ms_shutdown(self.handle)
-            self.handle = None
+            if rc != MS_EBUSY:
+                self.handle = None
             return rc
         return MS_OK
 
