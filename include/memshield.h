@@ -252,6 +252,7 @@ typedef struct ms_batch_config {
   uint32_t use_graph;    /* nonzero (default): launch through a captured CUDA graph */
   uint32_t grab;         /* pages a CTA claims per atomic; 0 = the context's tuned value */
   uint32_t ctas_per_sm;  /* persistent CTAs per SM; 0 = the tuned value (all that fit) */
+  uint32_t per_page_domain; /* nonzero: queue entries carry a domain each (32 B, ms_batch_add_dom) */
 } ms_batch_config;
 
 typedef struct ms_batch_stats {
@@ -267,6 +268,10 @@ int ms_batch_create(ms_ctx *ctx, const ms_batch_config *cfg, ms_batch **out);
 /* Append one request (op is bookkeeping: encryption = decryption).  Entries are
  * checked on the host (MS_EINVAL).  MS_EBUSY: the batch is full, submit first. */
 int ms_batch_add(ms_batch *batch, int op, const ms_page *pages, size_t n);
+/* Same with a domain (client PID) per page; the batch must have been created
+ * with per_page_domain (else MS_EINVAL).  ms_batch_add on such a batch uses
+ * the context's domain. */
+int ms_batch_add_dom(ms_batch *batch, int op, const ms_page_dom *pages, size_t n);
 /* Append n_requests requests at once: request r is op ops[r] on
  * pages[offsets[r] .. offsets[r + 1]) (offsets has n_requests + 1 entries).
  * Stops at the first request that fails (MS_EBUSY when the batch is full);

@@ -68,10 +68,15 @@ void batch_params(const ms_batch *b, QueueKernel *k, int *grid, int *grab) {
   *grab = b->cfg.grab ? (int)b->cfg.grab : c->qtune.grab;
 }
 
+size_t item_bytes(const ms_batch *b) { return b->cfg.per_page_domain ? sizeof(ms_page_dom) : sizeof(ms_page); }
+
 QueueArgs queue_args(const ms_batch *b, const QBuf &q, int grab) {
   const ms_ctx *c = b->ctx;
   QueueArgs a{};
-  a.items = reinterpret_cast<const ms_page *>(q.d + kHeader);
+  if (b->cfg.per_page_domain)
+    a.ditems = reinterpret_cast<const ms_page_dom *>(q.d + kHeader);
+  else
+    a.items = reinterpret_cast<const ms_page *>(q.d + kHeader);
   a.count = reinterpret_cast<const uint32_t *>(q.d);
   a.head = reinterpret_cast<uint32_t *>(q.d + kHeadOffset);
   a.grab = (uint32_t)grab;
@@ -113,6 +118,46 @@ cudaError_t capture(ms_batch *b, QBuf &q) {
   return e;
 }
 
+// Append one request given as ms_page (domain = the context's) or ms_page_dom.
+template <typename E>
+int batch_append(ms_batch *b, int op, const E *pages, size_t n) {
+  if (!b) return MS_EINVAL;
+  ms_ctx *c = b->ctx;
+  if (!c || !c->alive) return MS_ENOTINIT;
+  if (op != MS_ENCRYPT && op != MS_DECRYPT) return MS_EINVAL;
+  if (n == 0) return MS_OK;
+  if (!pages) return MS_EINVAL;
+  constexpr bool kDom = sizeof(E) == sizeof(ms_page_dom);
+  if (kDom && !b->cfg.per_page_domain) return MS_EINVAL;
+  for (size_t i = 0; i < n; ++i)
+    if (pages[i].addr == 0 || (pages[i].addr & 15u)) return MS_EINVAL;
+  std::lock_guard<std::mutex> lk(b->mu);
+  QBuf &q = b->buf[b->cur];
+  if (q.n + n > b->cfg.capacity) return MS_EBUSY;  // submit first
+  if (q.inflight) {  // the GPU may still read this buffer's previous batch
+    DeviceGuard g(c->device);
+    int rc = wait_event(c, q.done, c->cfg.timeout_ms);
+    if (rc != MS_OK) return rc;
+    q.inflight = false;
+  }
+  uint8_t *dst = q.h + kHeader + item_bytes(b) * q.n;
+  if (kDom || !b->cfg.per_page_domain) {
+    std::memcpy(dst, pages, n * sizeof(E));
+  } else {  // ms_page into a per-page-domain queue: the context's domain
+    ms_page_dom *d = reinterpret_cast<ms_page_dom *>(dst);
+    for (size_t i = 0; i < n; ++i) {
+      d[i] = ms_page_dom{};
+      d[i].addr = pages[i].addr;
+      d[i].page_id = pages[i].page_id;
+      d[i].domain = c->cfg.domain;
+    }
+  }
+  q.n += n;
+  b->stats.requests += 1;
+  b->stats.pages += n;
+  return MS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -140,7 +185,7 @@ int ms_batch_create(ms_ctx *c, const ms_batch_config *cfg_in, ms_batch **out) {
   b->ctx = c;
   b->cfg = cfg;
   DeviceGuard g(c->device);
-  const size_t bytes = kHeader + sizeof(ms_page) * (size_t)cfg.capacity;
+  const size_t bytes = kHeader + (cfg.per_page_domain ? sizeof(ms_page_dom) : sizeof(ms_page)) * (size_t)cfg.capacity;
   for (QBuf &q : b->buf) {
     cudaError_t e = cudaHostAlloc(&q.h, bytes, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc(&q.d, bytes);
@@ -156,29 +201,9 @@ int ms_batch_create(ms_ctx *c, const ms_batch_config *cfg_in, ms_batch **out) {
   return MS_OK;
 }
 
-int ms_batch_add(ms_batch *b, int op, const ms_page *pages, size_t n) {
-  if (!b) return MS_EINVAL;
-  ms_ctx *c = b->ctx;
-  if (!c || !c->alive) return MS_ENOTINIT;
-  if (op != MS_ENCRYPT && op != MS_DECRYPT) return MS_EINVAL;
-  if (n == 0) return MS_OK;
-  if (!pages) return MS_EINVAL;
-  for (size_t i = 0; i < n; ++i)
-    if (pages[i].addr == 0 || (pages[i].addr & 15u)) return MS_EINVAL;
-  std::lock_guard<std::mutex> lk(b->mu);
-  QBuf &q = b->buf[b->cur];
-  if (q.n + n > b->cfg.capacity) return MS_EBUSY;  // submit first
-  if (q.inflight) {  // the GPU may still read this buffer's previous batch
-    DeviceGuard g(c->device);
-    int rc = wait_event(c, q.done, c->cfg.timeout_ms);
-    if (rc != MS_OK) return rc;
-    q.inflight = false;
-  }
-  std::memcpy(q.h + kHeader + sizeof(ms_page) * q.n, pages, n * sizeof(ms_page));
-  q.n += n;
-  b->stats.requests += 1;
-  b->stats.pages += n;
-  return MS_OK;
+int ms_batch_add(ms_batch *b, int op, const ms_page *pages, size_t n) { return batch_append(b, op, pages, n); }
+int ms_batch_add_dom(ms_batch *b, int op, const ms_page_dom *pages, size_t n) {
+  return batch_append(b, op, pages, n);
 }
 
 int ms_batch_add_requests(ms_batch *b, size_t n_requests, const int *ops, const uint64_t *offsets,
@@ -206,7 +231,7 @@ int ms_batch_submit(ms_batch *b) {
   DeviceGuard g(c->device);
   const uint32_t count = (uint32_t)q.n;
   std::memcpy(q.h, &count, sizeof(count));
-  cudaError_t e = cudaMemcpyAsync(q.d, q.h, kHeader + sizeof(ms_page) * q.n, cudaMemcpyHostToDevice, c->stream);
+  cudaError_t e = cudaMemcpyAsync(q.d, q.h, kHeader + item_bytes(b) * q.n, cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);
   if (b->cfg.use_graph) {
     if (!q.exec || q.exec_key != c->tune_gen.load()) {

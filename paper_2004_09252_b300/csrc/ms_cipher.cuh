@@ -329,6 +329,7 @@ __global__ void __launch_bounds__(512) k_pages(const PageArgs a) {
 // Arguments of the persistent queue kernel.
 struct QueueArgs {
   const ms_page *items;   // the device work queue: one entry per page
+  const ms_page_dom *ditems;  // the same with a domain per entry (DOM instances)
   const uint32_t *count;  // number of valid entries (device word written with the items)
   uint32_t *head;         // next unclaimed entry; 0 at launch
   uint32_t grab;          // pages a CTA claims per atomic on head
@@ -344,7 +345,7 @@ struct QueueArgs {
 // time (TPP = 64 / BPT threads per page), until the head passes the count.
 // The head only grows, so every CTA leaves after at most count / grab + 1
 // claims; nothing waits.
-template <int ROUNDS, int BPT, int UNR, int POL, bool HOIST = false>
+template <int ROUNDS, int BPT, int UNR, int POL, bool HOIST = false, bool DOM = false>
 __global__ void __launch_bounds__(512) k_queue(const QueueArgs q) {
   constexpr uint32_t TPP = 64 / BPT;
   __shared__ uint32_t s_base;
@@ -363,7 +364,15 @@ __global__ void __launch_bounds__(512) k_queue(const QueueArgs q) {
     if (base >= n) break;
     const uint32_t end = min(base + q.grab, n);
     for (uint32_t p = base + lp; p < end; p += pages_per_pass) {
-      const ms_page e = q.items[p];
+      ms_page e;
+      if (DOM) {
+        const ms_page_dom ed = q.ditems[p];
+        e.addr = ed.addr;
+        e.page_id = ed.page_id;
+        s.n2 = ed.domain;
+      } else {
+        e = q.items[p];
+      }
       if (!entry_ok(e.addr)) {
         if (t == 0) atomicOr(q.status, kStatusBadEntry);
         continue;

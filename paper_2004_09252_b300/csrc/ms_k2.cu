@@ -6,7 +6,10 @@ namespace {
 
 template <int R, int B, int U, int P, bool H>
 cudaError_t launch_k2(const QueueArgs &q, int grid, int tpc, cudaStream_t s) {
-  k_queue<R, B, U, P, H><<<grid, tpc, 0, s>>>(q);
+  if (q.ditems)
+    k_queue<R, B, U, P, H, true><<<grid, tpc, 0, s>>>(q);
+  else
+    k_queue<R, B, U, P, H, false><<<grid, tpc, 0, s>>>(q);
   return cudaGetLastError();
 }
 

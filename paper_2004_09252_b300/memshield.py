@@ -66,6 +66,7 @@ class ms_batch_config(ctypes.Structure):
         ("use_graph", ctypes.c_uint32),
         ("grab", ctypes.c_uint32),
         ("ctas_per_sm", ctypes.c_uint32),
+        ("per_page_domain", ctypes.c_uint32),
     ]
 
 
@@ -167,6 +168,7 @@ def _load():
         "ms_batch_config_default": (None, [ctypes.POINTER(ms_batch_config)]),
         "ms_batch_create": (I, [P, ctypes.POINTER(ms_batch_config), ctypes.POINTER(P)]),
         "ms_batch_add": (I, [P, I, P, S]),
+        "ms_batch_add_dom": (I, [P, I, P, S]),
         "ms_batch_submit": (I, [P]),
         "ms_batch_add_requests": (I, [P, S, P, P, P, ctypes.POINTER(ctypes.c_size_t)]),
         "ms_batch_get_stats": (I, [P, ctypes.POINTER(ms_batch_stats)]),
@@ -340,8 +342,9 @@ class Context:
     def tune_load(self, path: str) -> int:
         return _lib.ms_tune_load(self.handle, path.encode())
 
-    def batch(self, capacity: int = 0, use_graph: bool = True, grab: int = 0, ctas_per_sm: int = 0) -> "Batch":
-        return Batch(self, capacity, use_graph, grab, ctas_per_sm)
+    def batch(self, capacity: int = 0, use_graph: bool = True, grab: int = 0, ctas_per_sm: int = 0,
+              per_page_domain: bool = False) -> "Batch":
+        return Batch(self, capacity, use_graph, grab, ctas_per_sm, per_page_domain)
 
     def get_shape(self) -> dict:
         sh = ms_shape()
@@ -391,7 +394,7 @@ class Batch:
     """An ms_batch: requests queued on the host, drained on the GPU by the persistent kernel."""
 
     def __init__(self, ctx: Context, capacity: int = 0, use_graph: bool = True, grab: int = 0,
-                 ctas_per_sm: int = 0):
+                 ctas_per_sm: int = 0, per_page_domain: bool = False):
         cfg = ms_batch_config()
         _lib.ms_batch_config_default(ctypes.byref(cfg))
         if capacity:
@@ -399,6 +402,7 @@ class Batch:
         cfg.use_graph = 1 if use_graph else 0
         cfg.grab = grab
         cfg.ctas_per_sm = ctas_per_sm
+        cfg.per_page_domain = 1 if per_page_domain else 0
         h = ctypes.c_void_p()
         _check(_lib.ms_batch_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "ms_batch_create")
         self.handle = h.value
@@ -410,6 +414,14 @@ class Batch:
         rc = _lib.ms_batch_add(self.handle, op, pages.ctypes.data, pages.size)
         if rc not in (MS_OK, MS_EBUSY):
             raise MemShieldError(rc, "ms_batch_add")
+        return rc
+
+    def add_dom(self, op: int, pages: np.ndarray) -> int:
+        """Queue one request with a domain per page; returns the status (MS_EBUSY when full)."""
+        pages = np.ascontiguousarray(pages, dtype=PAGE_DOM_DTYPE)
+        rc = _lib.ms_batch_add_dom(self.handle, op, pages.ctypes.data, pages.size)
+        if rc not in (MS_OK, MS_EBUSY):
+            raise MemShieldError(rc, "ms_batch_add_dom")
         return rc
 
     def add_requests(self, ops: np.ndarray, offsets: np.ndarray, pages: np.ndarray, first: int = 0,

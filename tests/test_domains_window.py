@@ -103,3 +103,29 @@ def test_window_rejects_bad_configs(ms, key1):
             srv.run_window_clients(4, 1, [(1, 0, 32, tr), (2, 16, 32, tr)])   # overlapping clients
         with pytest.raises(ms.MemShieldError):
             srv.run_window_clients(4, 1, [(1, 0, 32, np.array([40], dtype=np.uint64))])  # outside the client
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batched_form_with_per_page_domains(ms, key1, use_graph):
+    n_slots, n = 1024, 700
+    plain = synth.page_bytes_fast(98, 0, n_slots)
+    d = torch.from_numpy(plain).cuda()
+    slots = synth.scattered_slots(99, n_slots, n).astype(np.uint64)
+    doms = (synth.splitmix64(100, 0, n) % np.uint64(4) + np.uint64(40)).astype(np.uint32)
+    doms[600:] = 5                                         # these go through ms_batch_add: context domain
+    with ms.Context(key1, stream=torch.cuda.current_stream(), domain=5) as ctx:
+        with ctx.batch(capacity=300, use_graph=use_graph, per_page_domain=True) as b:
+            for lo in range(0, 600, 50):
+                sel = slice(lo, lo + 50)
+                e = ms.pages_dom_array(d.data_ptr() + PAGE * slots[sel], slots[sel], doms[sel])
+                if b.add_dom(ms.MS_ENCRYPT, e) == ms.MS_EBUSY:
+                    b.submit()
+                    assert b.add_dom(ms.MS_ENCRYPT, e) == ms.MS_OK
+            b.submit()
+            assert b.add(ms.MS_ENCRYPT, ms.pages_array(d.data_ptr() + PAGE * slots[600:], slots[600:])) == ms.MS_OK
+            b.submit()
+            ctx.sync_checked()
+        with ctx.batch(capacity=16) as plain_batch:
+            with pytest.raises(ms.MemShieldError):
+                plain_batch.add_dom(ms.MS_ENCRYPT, ms.pages_dom_array([d.data_ptr()], [0], [1]))
+    assert np.array_equal(d.cpu().numpy(), oracle_by_domain(key1, plain, slots, slots, doms))
