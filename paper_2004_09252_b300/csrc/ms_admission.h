@@ -1,0 +1,123 @@
+// Admission policy of the served form, in plain C++ (no CUDA), so that the
+// host logic can be tested on its own.
+//
+// State: a ring of S staging slots (waves take contiguous runs of slots and
+// are released in the order they were issued) and a per-page mark of the
+// pages that belong to an admitted, not yet completed wave.
+//
+// form(): queued requests are scanned in arrival order (at most `window` of
+// them) and admitted into one wave while the wave and the ring have room:
+//   - a request with a page already in flight (or in this wave) is skipped,
+//     and its pages are blocked for the rest of the scan, so a later request
+//     that shares one of them cannot overtake it;
+//   - running out of ring room ends the scan (no overtaking for room, so a
+//     large request is not starved by small ones);
+//   - in one-per-launch mode a wave holds one request.
+// A wave that does not fit before the end of the ring starts at slot 0, and
+// the skipped tail counts as used until the wave is released.
+#pragma once
+
+#include <algorithm>
+#include <cstdint>
+#include <deque>
+#include <vector>
+
+namespace ms {
+
+struct AdmittedWave {
+  std::vector<uint64_t> tickets;
+  uint32_t pos = 0;   // first staging slot
+  uint32_t len = 0;   // pages
+  uint32_t span = 0;  // ring slots consumed: len plus the skipped tail
+};
+
+class Admission {
+ public:
+  Admission(uint32_t slots, uint32_t max_wave_pages, bool one_per_launch, uint64_t n_pages, size_t window)
+      : S_(slots), max_wave_(max_wave_pages), one_(one_per_launch), window_(window), busy_(n_pages, 0) {}
+
+  uint32_t slots() const { return S_; }
+  uint32_t used() const { return used_; }
+  uint64_t conflict_waits = 0, budget_waits = 0;
+
+  // pages_of(ticket) returns the request's page list (a container of uint64_t).
+  template <typename PagesOf>
+  bool form(std::deque<uint64_t> &queue, PagesOf pages_of, AdmittedWave &w) {
+    if (used_ == 0) head_ = 0;  // nothing in flight: the whole ring is free from slot 0
+    uint32_t pos = head_, waste = 0, len = 0;
+    const size_t window = std::min(queue.size(), window_);
+    std::vector<uint8_t> taken(window, 0);
+    std::vector<uint64_t> blocked;
+    size_t n_taken = 0;
+    for (size_t i = 0; i < window; ++i) {
+      const auto &pages = pages_of(queue[i]);
+      const uint32_t n = (uint32_t)pages.size();
+      if (one_ && n_taken == 1) break;
+      if (len + n > max_wave_ && n_taken > 0) break;
+      uint32_t p = pos, wst = waste;
+      if (len == 0 && p + n > S_) {  // wrap to slot 0
+        wst = S_ - p;
+        p = 0;
+      }
+      if (p + len + n > S_ || used_ + wst + len + n > S_) {
+        ++budget_waits;
+        break;
+      }
+      bool conflict = false;
+      for (uint64_t pg : pages)
+        if (busy_[pg]) {
+          conflict = true;
+          break;
+        }
+      if (conflict) {
+        ++conflict_waits;
+        for (uint64_t pg : pages)
+          if (!busy_[pg]) {
+            busy_[pg] = 2;  // blocked for the rest of this scan
+            blocked.push_back(pg);
+          }
+        continue;
+      }
+      for (uint64_t pg : pages) busy_[pg] = 1;
+      pos = p;
+      waste = wst;
+      len += n;
+      w.tickets.push_back(queue[i]);
+      taken[i] = 1;
+      ++n_taken;
+    }
+    for (uint64_t pg : blocked) busy_[pg] = 0;
+    if (n_taken == 0) return false;
+    // drop the admitted tickets from the scanned prefix, keeping the others in order
+    std::vector<uint64_t> keep;
+    keep.reserve(window - n_taken);
+    for (size_t i = 0; i < window; ++i)
+      if (!taken[i]) keep.push_back(queue[i]);
+    queue.erase(queue.begin(), queue.begin() + (long)window);
+    for (size_t i = keep.size(); i-- > 0;) queue.push_front(keep[i]);
+    w.pos = pos;
+    w.len = len;
+    w.span = waste + len;
+    head_ = pos + len;
+    used_ += w.span;
+    return true;
+  }
+
+  // A completed wave: its pages leave the in-flight set and its slots are
+  // freed.  Waves must be released in the order form() returned them.
+  template <typename PagesOf>
+  void release(const AdmittedWave &w, PagesOf pages_of) {
+    for (uint64_t t : w.tickets)
+      for (uint64_t pg : pages_of(t)) busy_[pg] = 0;
+    used_ -= w.span;
+  }
+
+ private:
+  uint32_t S_, max_wave_;
+  bool one_;
+  size_t window_;
+  std::vector<uint8_t> busy_;
+  uint32_t head_ = 0, used_ = 0;
+};
+
+}  // namespace ms

@@ -25,6 +25,7 @@
 #include <thread>
 #include <vector>
 
+#include "ms_admission.h"
 #include "ms_internal.h"
 
 using namespace ms;
@@ -141,9 +142,7 @@ class CopyPool {
   bool stop_ = false;
 };
 
-struct Wave {
-  std::vector<uint64_t> tickets;
-  uint32_t pos = 0, len = 0, span = 0;  // first slot, pages, ring slots consumed (len + skipped tail)
+struct Wave : ms::AdmittedWave {
   cudaEvent_t ev_h2d = nullptr, ev_done = nullptr;
 };
 
@@ -163,8 +162,7 @@ struct ms_server {
   std::condition_variable qcv;
   std::deque<uint64_t> incoming;
   std::atomic<uint64_t> next_ticket{0};
-  std::vector<uint8_t> busy;  // per working-set page: in a queued wave
-  uint32_t ring_head = 0, ring_used = 0;
+  ms::Admission *adm = nullptr;  // staging ring and in-flight pages (guarded by qmu)
   std::deque<Wave> inflight;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
   uint64_t wave_seq = 0;
@@ -198,76 +196,17 @@ void atomic_max(std::atomic<uint64_t> &a, uint64_t v) {
 
 }  // namespace
 
-// Admission.  Queued requests are scanned in arrival order (at most
-// kScanWindow of them per wave) and admitted while the wave and the staging
-// ring have room.  A request with a page already in flight (or in this wave)
-// is skipped, and its pages are blocked for the rest of the scan, so a later
-// request sharing one of them cannot overtake it; requests on other pages
-// still join.  Running out of staging room ends the scan (no overtaking for
-// room, so large requests are not starved).
+// Admission (see ms_admission.h): at most kScanWindow queued requests are
+// considered per wave.
 constexpr size_t kScanWindow = 4096;
 
 bool ms_server::form_wave(Wave &w) {
   std::lock_guard<std::mutex> lk(qmu);
-  if (ring_used == 0) ring_head = 0;  // nothing in flight: the whole ring is free from slot 0
-  uint32_t pos = ring_head, waste = 0, len = 0;
-  const size_t window = std::min(incoming.size(), kScanWindow);
-  std::vector<uint8_t> taken(window, 0);
-  std::vector<uint64_t> blocked;
-  size_t n_taken = 0;
-  for (size_t i = 0; i < window; ++i) {
-    Req &r = slot(incoming[i]);
-    const uint32_t n = (uint32_t)r.pages.size();
-    if (cfg.mode == MS_SERVE_ONE_PER_LAUNCH && n_taken == 1) break;
-    if (len + n > cfg.max_wave_pages) {
-      if (n_taken > 0) break;
-    }
-    // contiguous room in the ring: wrap to slot 0 if the tail is too short
-    uint32_t p = pos, wst = waste;
-    if (len == 0 && p + n > S) {
-      wst = S - p;
-      p = 0;
-    }
-    if (p + len + n > S || ring_used + wst + len + n > S) {
-      st_budget.fetch_add(1);
-      break;
-    }
-    bool conflict = false;
-    for (uint64_t pg : r.pages)
-      if (busy[pg]) {
-        conflict = true;
-        break;
-      }
-    if (conflict) {
-      st_conflict.fetch_add(1);
-      for (uint64_t pg : r.pages)
-        if (!busy[pg]) {
-          busy[pg] = 2;  // blocked for the rest of this scan
-          blocked.push_back(pg);
-        }
-      continue;
-    }
-    for (uint64_t pg : r.pages) busy[pg] = 1;
-    pos = p;
-    waste = wst;
-    len += n;
-    w.tickets.push_back(incoming[i]);
-    taken[i] = 1;
-    ++n_taken;
-  }
-  for (uint64_t pg : blocked) busy[pg] = 0;
-  if (n_taken == 0) return false;
-  // drop the admitted tickets from the scanned prefix, keeping the others in order
-  std::vector<uint64_t> keep;
-  keep.reserve(window - n_taken);
-  for (size_t i = 0; i < window; ++i)
-    if (!taken[i]) keep.push_back(incoming[i]);
-  incoming.erase(incoming.begin(), incoming.begin() + (long)window);
-  for (size_t i = keep.size(); i-- > 0;) incoming.push_front(keep[i]);
-  w.pos = pos;
-  w.len = len;
-  w.span = waste + len;
-  return true;
+  const bool ok = adm->form(incoming, [&](uint64_t t) -> const std::vector<uint64_t> & { return slot(t).pages; }, w);
+  st_budget.store(adm->budget_waits);
+  st_conflict.store(adm->conflict_waits);
+  if (ok) atomic_max(st_maxstaged, adm->used());
+  return ok;
 }
 
 int ms_server::issue(Wave &w) {
@@ -327,9 +266,6 @@ int ms_server::issue(Wave &w) {
   if (e == cudaSuccess && cfg.zero_staging && !zc) e = cudaMemsetAsync(d_stage + off, 0, bytes, sw);
   if (e == cudaSuccess) e = cudaEventRecord(w.ev_done, sw);
   if (e != cudaSuccess) return cuda_fail(ctx, e);
-  ring_head = w.pos + w.len;
-  ring_used += w.span;
-  atomic_max(st_maxstaged, ring_used);
   st_waves.fetch_add(1);
   atomic_max(st_maxreq, w.tickets.size());
   atomic_max(st_maxpages, w.len);
@@ -355,9 +291,8 @@ void ms_server::complete(Wave &w) {
   st_scatter_ns.fetch_add(t - ts);
   uint64_t pages = 0;
   {
-    std::lock_guard<std::mutex> lk(qmu);  // busy[] is shared with admission
-    for (uint64_t tk : w.tickets)
-      for (uint64_t pg : slot(tk).pages) busy[pg] = 0;
+    std::lock_guard<std::mutex> lk(qmu);  // the admission state is shared with form_wave
+    adm->release(w, [&](uint64_t t) -> const std::vector<uint64_t> & { return slot(t).pages; });
   }
   for (uint64_t tk : w.tickets) {
     Req &r = slot(tk);
@@ -366,7 +301,6 @@ void ms_server::complete(Wave &w) {
     if (r.lat_out) *r.lat_out = (double)((int64_t)(t - r.t_sched_ns)) * 1e-9;
     r.state.store(kDone, std::memory_order_release);
   }
-  ring_used -= w.span;
   ev_pool.push_back({w.ev_h2d, w.ev_done});
   st_req.fetch_add(w.tickets.size());
   st_pages.fetch_add(pages);
@@ -482,6 +416,7 @@ void ms_server_config_default(ms_server_config *cfg) {
 
 static void free_server(ms_server *s) {
   if (s->pool) delete s->pool;
+  if (s->adm) delete s->adm;
   for (auto &p : s->ev_pool) {
     cudaEventDestroy(p.first);
     cudaEventDestroy(p.second);
@@ -548,7 +483,7 @@ int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_serv
   }
   try {
     s->reqs = std::vector<Req>(cfg.max_pending);
-    s->busy.assign(n_pages, 0);
+    s->adm = new ms::Admission(S, cfg.max_wave_pages, cfg.mode == MS_SERVE_ONE_PER_LAUNCH, n_pages, kScanWindow);
     s->pool = new CopyPool((int)cfg.copy_threads);
     s->th = std::thread([s] { s->loop(); });
   } catch (...) {
