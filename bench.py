@@ -248,8 +248,7 @@ def run_ours(args):
     lst = torch.from_numpy(ms.pages_array(d.data_ptr() + PAGE * ids, ids).view(np.uint8)).to(f"cuda:{dev}")
     ctx = ms.Context(key, device=dev, stream=stream.cuda_stream)
     if args.shape:
-        b, t, u, p = (int(x) for x in args.shape.split(","))
-        ctx.set_shape(b, t, u, p)
+        ctx.set_shape(*(int(x) for x in args.shape.split(",")))
     shape = ctx.get_shape()
 
     def barrier():
@@ -757,7 +756,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--pages", type=int, default=BULK_PAGES,
                     help="pages in the buffer (default: the 1 GiB bulk workload; smaller only for profiling)")
-    ap.add_argument("--shape", default="", help="K1 shape override: bpt,tpc,unroll,rot_policy")
+    ap.add_argument("--shape", default="", help="K1 shape override: bpt,tpc,unroll,rot_policy[,hoist]")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the short serving summary in the bulk line")
