@@ -88,7 +88,7 @@ typedef struct ms_config {
   uint32_t rounds;             /* 20 (default), or 8 / 12 */
   uint32_t list_capacity;      /* entries per host-list staging slot (default 65536) */
   uint32_t timeout_ms;         /* bound on every host-side wait (default 10000) */
-  uint32_t blocks_per_thread;  /* 0 = default (2); else 1, 2 or 4 keystream blocks per thread */
+  uint32_t blocks_per_thread;  /* 0 = default (4); else 1, 2 or 4 keystream blocks per thread */
   uint32_t threads_per_cta;    /* 0 = default (128); else 128, 256 or 512 */
   uint32_t dr_unroll;          /* 0 = default (rounds/2); else double rounds per loop trip: 1, 2 or rounds/2 */
   uint32_t check_duplicates;   /* nonzero: host-list calls reject a page address listed twice */

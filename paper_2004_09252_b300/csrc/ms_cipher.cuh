@@ -190,38 +190,38 @@ __device__ __forceinline__ Prelude make_prelude(const BlockSeed &s, const MulCon
   return p;
 }
 
-// xor_block with the first double round started from a Prelude.  The
+// Keystream block `counter` XORed into the 64 bytes `d` already loaded (and
+// stored to dst), with the first double round started from a Prelude.  The
 // remaining double rounds are fully unrolled.
 template <int ROUNDS, int POL>
-__device__ __forceinline__ void xor_block_hoisted(uint4 *__restrict__ dst, const BlockSeed &s, const Prelude &p,
-                                                  uint32_t counter, const MulConsts &mc) {
-  uint4 d0 = __ldcs(dst + 0), d1 = __ldcs(dst + 1), d2 = __ldcs(dst + 2), d3 = __ldcs(dst + 3);
+__device__ __forceinline__ void xor_loaded_hoisted(uint4 *__restrict__ dst, uint4 (&d)[4], const BlockSeed &s,
+                                                   const Prelude &p, uint32_t counter, const MulConsts &mc) {
   uint32_t x0, x4, x8, x12;
   uint32_t x1, x2, x3, x5 = p.x5, x6, x7, x9 = p.x9, x10 = p.x10, x11, x13, x14 = p.x14, x15 = p.x15;
   {  // column QR (0, 4, 8, 12), the only one that sees the counter
-    uint32_t a = p.a0, b = s.k[0], c = s.k[4], d = counter;
-    d = rotl16<POL>(d ^ a);
-    c += d; b = rotl12<POL, true>(b ^ c, mc);
-    a += b; d = rotl8<POL>(d ^ a);
-    c += d; b = rotl7<POL, true>(b ^ c, mc);
-    x0 = a; x4 = b; x8 = c; x12 = d;
+    uint32_t a = p.a0, b = s.k[0], c = s.k[4], dd = counter;
+    dd = rotl16<POL>(dd ^ a);
+    c += dd; b = rotl12<POL, true>(b ^ c, mc);
+    a += b; dd = rotl8<POL>(dd ^ a);
+    c += dd; b = rotl7<POL, true>(b ^ c, mc);
+    x0 = a; x4 = b; x8 = c; x12 = dd;
   }
   // diagonal round
   quarter_round<POL, false>(x0, x5, x10, x15, mc);
   {  // (1, 6, 11, 12): a = x1 + x6 precomputed
-    uint32_t a = p.da1, b = p.x6, c = p.x11, d = x12;
-    d = rotl16<POL>(d ^ a);
-    c += d; b = rotl12<POL, false>(b ^ c, mc);
-    a += b; d = rotl8<POL>(d ^ a);
-    c += d; b = rotl7<POL, false>(b ^ c, mc);
-    x1 = a; x6 = b; x11 = c; x12 = d;
+    uint32_t a = p.da1, b = p.x6, c = p.x11, dd = x12;
+    dd = rotl16<POL>(dd ^ a);
+    c += dd; b = rotl12<POL, false>(b ^ c, mc);
+    a += b; dd = rotl8<POL>(dd ^ a);
+    c += dd; b = rotl7<POL, false>(b ^ c, mc);
+    x1 = a; x6 = b; x11 = c; x12 = dd;
   }
   {  // (2, 7, 8, 13): a = x2 + x7 and d = (x13 ^ a) <<< 16 precomputed
-    uint32_t a = p.da2, b = p.x7, c = x8, d = p.dd2;
-    c += d; b = rotl12<POL, false>(b ^ c, mc);
-    a += b; d = rotl8<POL>(d ^ a);
-    c += d; b = rotl7<POL, false>(b ^ c, mc);
-    x2 = a; x7 = b; x8 = c; x13 = d;
+    uint32_t a = p.da2, b = p.x7, c = x8, dd = p.dd2;
+    c += dd; b = rotl12<POL, false>(b ^ c, mc);
+    a += b; dd = rotl8<POL>(dd ^ a);
+    c += dd; b = rotl7<POL, false>(b ^ c, mc);
+    x2 = a; x7 = b; x8 = c; x13 = dd;
   }
   x3 = p.x3;
   quarter_round<POL, false>(x3, x4, x9, x14, mc);
@@ -236,11 +236,11 @@ __device__ __forceinline__ void xor_block_hoisted(uint4 *__restrict__ dst, const
     quarter_round<POL, false>(x2, x7, x8, x13, mc);
     quarter_round<POL, false>(x3, x4, x9, x14, mc);
   }
-  d0.x ^= x0 + kSigma0;  d0.y ^= x1 + kSigma1;  d0.z ^= x2 + kSigma2;  d0.w ^= x3 + kSigma3;
-  d1.x ^= x4 + s.k[0];   d1.y ^= x5 + s.k[1];   d1.z ^= x6 + s.k[2];   d1.w ^= x7 + s.k[3];
-  d2.x ^= x8 + s.k[4];   d2.y ^= x9 + s.k[5];   d2.z ^= x10 + s.k[6];  d2.w ^= x11 + s.k[7];
-  d3.x ^= x12 + counter; d3.y ^= x13 + s.n0;    d3.z ^= x14 + s.n1;    d3.w ^= x15 + s.n2;
-  __stcs(dst + 0, d0); __stcs(dst + 1, d1); __stcs(dst + 2, d2); __stcs(dst + 3, d3);
+  d[0].x ^= x0 + kSigma0;  d[0].y ^= x1 + kSigma1;  d[0].z ^= x2 + kSigma2;  d[0].w ^= x3 + kSigma3;
+  d[1].x ^= x4 + s.k[0];   d[1].y ^= x5 + s.k[1];   d[1].z ^= x6 + s.k[2];   d[1].w ^= x7 + s.k[3];
+  d[2].x ^= x8 + s.k[4];   d[2].y ^= x9 + s.k[5];   d[2].z ^= x10 + s.k[6];  d[2].w ^= x11 + s.k[7];
+  d[3].x ^= x12 + counter; d[3].y ^= x13 + s.n0;    d[3].z ^= x14 + s.n1;    d[3].w ^= x15 + s.n2;
+  __stcs(dst + 0, d[0]); __stcs(dst + 1, d[1]); __stcs(dst + 2, d[2]); __stcs(dst + 3, d[3]);
 }
 
 // All blocks `t + b * TPP` (b < BPT) of one page for one thread; with HOIST the
@@ -249,11 +249,22 @@ template <int ROUNDS, int BPT, int UNR, int POL, bool HOIST>
 __device__ __forceinline__ void page_blocks(uint4 *__restrict__ pg, const BlockSeed &s, uint32_t t, uint32_t tpp,
                                             const MulConsts &mc) {
   if (HOIST) {
+    // Software pipeline: the next block's 64 bytes are loaded while the
+    // current block's keystream is computed, so the loads are in flight
+    // however the compiler schedules the rounds.
+    uint4 cur[4], nxt[4];
+    const uint4 *src = pg + 4 * t;
+    cur[0] = __ldcs(src + 0); cur[1] = __ldcs(src + 1); cur[2] = __ldcs(src + 2); cur[3] = __ldcs(src + 3);
     const Prelude p = make_prelude<POL>(s, mc);
 #pragma unroll 1
     for (int b = 0; b < BPT; ++b) {
       const uint32_t j = t + b * tpp;
-      xor_block_hoisted<ROUNDS, POL>(pg + 4 * j, s, p, j, mc);
+      if (b + 1 < BPT) {
+        const uint4 *nsrc = pg + 4 * (j + tpp);
+        nxt[0] = __ldcs(nsrc + 0); nxt[1] = __ldcs(nsrc + 1); nxt[2] = __ldcs(nsrc + 2); nxt[3] = __ldcs(nsrc + 3);
+      }
+      xor_loaded_hoisted<ROUNDS, POL>(pg + 4 * j, cur, s, p, j, mc);
+      cur[0] = nxt[0]; cur[1] = nxt[1]; cur[2] = nxt[2]; cur[3] = nxt[3];
     }
   } else {
 #pragma unroll 1

