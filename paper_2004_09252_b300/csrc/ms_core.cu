@@ -270,6 +270,7 @@ int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg_in) {
   }
 #undef MS_TRY
 
+  c->shape_explicit = cfg.blocks_per_thread || cfg.threads_per_cta || cfg.dr_unroll;
   if (cfg.blocks_per_thread) c->tune.bpt = (int)cfg.blocks_per_thread;
   if (cfg.threads_per_cta) c->tune.tpc = (int)cfg.threads_per_cta;
   if (cfg.dr_unroll) c->tune.unr = (int)cfg.dr_unroll;
@@ -390,6 +391,7 @@ int ms_set_shape(ms_ctx *c, const ms_shape *sh) {
   if (!shape_available((int)c->cfg.rounds, t)) return MS_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
   c->tune = t;
+  c->shape_explicit = true;
   c->tune_gen.fetch_add(1);
   return MS_OK;
 }

@@ -58,6 +58,7 @@ struct ms_ctx {
   bool status_pending = false;       // that read was queued but not yet collected
   unsigned status_acc = 0;           // status bits collected by a call that then timed out
   ms::Tune tune;
+  bool shape_explicit = false;  // set by the caller (config, ms_set_shape, a loaded table): never adapted
   ms::QTune qtune;
   std::atomic<unsigned> tune_gen{0};  // bumped whenever tune/qtune change
   ms::ListSlot slots[ms::kListSlots];

@@ -83,7 +83,21 @@ cudaError_t launch_pages_shape(const PageArgs &a, int rounds, const Tune &t, boo
 }
 
 cudaError_t launch_pages(const ms_ctx *c, const PageArgs &a, cudaStream_t s) {
-  return launch_pages_shape(a, (int)c->cfg.rounds, c->tune, a.pages == nullptr && a.dpages == nullptr, s);
+  Tune t = c->tune;
+  // A launch too small to fill the GPU with the default shape gets one block
+  // per thread instead: 4x the threads, a quarter of the serial work per
+  // thread, so small requests finish sooner.  Shapes the caller chose are
+  // used as they are.
+  if (!c->shape_explicit && t.bpt > 1 && a.n_pages * (uint64_t)(64 / t.bpt) < (uint64_t)c->sm_count * 1024) {
+    Tune small;
+    small.bpt = 1;
+    small.tpc = 128;
+    small.unr = (int)c->cfg.rounds / 2;
+    small.pol = kRotPerm;
+    small.hoist = 0;
+    if (shape_available((int)c->cfg.rounds, small)) t = small;
+  }
+  return launch_pages_shape(a, (int)c->cfg.rounds, t, a.pages == nullptr && a.dpages == nullptr, s);
 }
 
 // Every compiled shape, for the autotuner.

@@ -214,6 +214,7 @@ int ms_tune_load(ms_ctx *c, const char *path) {
   if (!shape_available(rounds, t) || q.grab < 1 || q.grab > 4096 || q.ctas_per_sm < 0) return MS_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
   c->tune = t;
+  c->shape_explicit = true;
   c->qtune = q;
   c->tune_gen.fetch_add(1);
   return MS_OK;
