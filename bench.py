@@ -363,10 +363,13 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         threads = host_cores()
         v, npg, dt, passes = cpu_oracle_rate(args.cpu_seconds, threads)
+        v1, npg1, dt1, passes1 = cpu_oracle_rate(max(2.0, args.cpu_seconds / 4), 1)
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
                                 "sample": f"{npg} pages ({npg * PAGE / 2**20:.0f} MiB) of the bulk buffer, "
                                           f"{passes} encrypt passes in {dt:.1f} s, pages split over "
-                                          f"{threads} threads"}
+                                          f"{threads} threads",
+                                "single_core": {"value": round(v1, 4), "unit": "GB/s",
+                                                "sample": f"{npg1} pages, {passes1} passes in {dt1:.1f} s, 1 thread"}}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
