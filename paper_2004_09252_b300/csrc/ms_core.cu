@@ -1,5 +1,6 @@
 // Context lifecycle, key placement, the one-launch entry points, ms_sync and
 // the streamed host-page form.
+#include <errno.h>
 #include <sys/random.h>
 #include <time.h>
 
@@ -250,6 +251,7 @@ int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg_in) {
     size_t got = 0;
     while (got < MS_KEY_BYTES) {
       ssize_t r = getrandom(bounce + got, MS_KEY_BYTES - got, 0);
+      if (r < 0 && errno == EINTR) continue;
       if (r < 0) {
         explicit_bzero(bounce, MS_KEY_BYTES);
         cudaFreeHost(bounce);

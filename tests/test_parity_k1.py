@@ -258,3 +258,23 @@ def test_launch_size_beyond_grid_limit_is_rejected_before_launch(ms, key1):
         assert e.value.code == ms.MS_ECUDA and ctx.last_cuda_error() == 9   # cudaErrorInvalidConfiguration
         ctx.sync_checked()
         assert int(d.sum()) == 0
+
+
+def test_random_key_from_the_os(ms):
+    """key = NULL draws the key with getrandom (Sec. 4.4): two contexts give
+    different ciphertexts, each decrypts its own, and neither is the plaintext."""
+    n = 8
+    plain = synth.page_bytes(140, 0, n)
+    ids = np.arange(n, dtype=np.uint64)
+    outs = []
+    for _ in range(2):
+        d = dev(plain)
+        with ms.Context(None, stream=torch.cuda.current_stream().cuda_stream) as ctx:
+            ctx.encrypt_pages(ms.pages_array(d.data_ptr() + PAGE * ids, ids))
+            ctx.sync_checked()
+            outs.append(d.cpu().numpy())
+            ctx.decrypt_pages(ms.pages_array(d.data_ptr() + PAGE * ids, ids))
+            ctx.sync_checked()
+            assert np.array_equal(d.cpu().numpy(), plain)
+    assert not np.array_equal(outs[0], outs[1])
+    assert not np.array_equal(outs[0], plain)
