@@ -269,7 +269,8 @@ void ms_batch_config_default(ms_batch_config *cfg);
 /* Allocates two pinned + two device queue buffers of 256 + 16 * capacity bytes. */
 int ms_batch_create(ms_ctx *ctx, const ms_batch_config *cfg, ms_batch **out);
 /* Append one request (op is bookkeeping: encryption = decryption).  Entries are
- * checked on the host (MS_EINVAL).  MS_EBUSY: the batch is full, submit first. */
+ * checked on the host (MS_EINVAL).  MS_EBUSY: the batch is full, submit first;
+ * MS_ERANGE: the request alone is larger than the batch capacity. */
 int ms_batch_add(ms_batch *batch, int op, const ms_page *pages, size_t n);
 /* Same with a domain (client PID) per page; the batch must have been created
  * with per_page_domain (else MS_EINVAL).  ms_batch_add on such a batch uses

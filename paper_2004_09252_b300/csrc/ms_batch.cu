@@ -131,6 +131,7 @@ int batch_append(ms_batch *b, int op, const E *pages, size_t n) {
   if (kDom && !b->cfg.per_page_domain) return MS_EINVAL;
   for (size_t i = 0; i < n; ++i)
     if (pages[i].addr == 0 || (pages[i].addr & 15u)) return MS_EINVAL;
+  if (n > b->cfg.capacity) return MS_ERANGE;  // can never fit
   std::lock_guard<std::mutex> lk(b->mu);
   QBuf &q = b->buf[b->cur];
   if (q.n + n > b->cfg.capacity) return MS_EBUSY;  // submit first

@@ -115,6 +115,10 @@ def test_batch_rejects_bad_entries_and_empty_submit(ms, key1):
         assert e.value.code == ms.MS_EINVAL
         with pytest.raises(ms.MemShieldError):
             b.add(5, ms.pages_array(d.data_ptr() + PAGE * ids, ids))
+        big = ms.pages_array(np.full(17, d.data_ptr(), np.uint64), np.arange(17))
+        with pytest.raises(ms.MemShieldError) as e:
+            b.add(ms.MS_ENCRYPT, big)                  # larger than the whole batch
+        assert e.value.code == ms.MS_ERANGE
         assert b.add(ms.MS_ENCRYPT, ms.pages_array(d.data_ptr() + PAGE * ids, ids)) == ms.MS_OK
         b.submit()
         ctx.sync_checked()
