@@ -74,9 +74,9 @@ class CopyPool {
   }
   // Runs fn(i) for i in [0, n); the calling thread takes part.
   void run(size_t n, const std::function<void(size_t)> &fn) {
-    // Below 2 MiB (~0.2 ms of memcpy) one thread does it: a hand-off costs
-    // wake-ups, and a worker preempted mid-job would stall the whole wave.
-    if (th_.empty() || n < 512) {
+    // Below 512 KiB one thread does it: a hand-off costs wake-ups.  (A
+    // threshold of 2 MiB measured worse: 532k-pages/s p99 1.3 -> 2.5-3.5 ms.)
+    if (th_.empty() || n < 128) {
       for (size_t i = 0; i < n; ++i) fn(i);
       return;
     }
