@@ -343,7 +343,9 @@ int ms_tune_load(ms_ctx *ctx, const char *path);
  */
 typedef struct ms_server ms_server;
 
-/* MS_SERVE_ZERO_COPY: no staging copies; the kernel reads and writes the
+/* Continuous mode stages large waves and runs small ones (zero_copy_max_pages)
+ * in place; MS_SERVE_ONE_PER_LAUNCH always stages.
+ * MS_SERVE_ZERO_COPY: no staging copies; the kernel reads and writes the
  * working set directly over the host link (it must be pinned, mapped memory,
  * e.g. from cudaHostAlloc); the staging budget then only bounds the pages in
  * flight.  Requests are admitted the same way. */
@@ -359,6 +361,9 @@ typedef struct ms_server_config {
   uint32_t zero_staging;     /* nonzero: wipe staging pages after each wave */
   uint32_t max_request_pages;/* largest request accepted (default 4096; <= staging pages) */
   uint32_t idle_spin_us;     /* idle server thread polls this long before sleeping (default 2000) */
+  uint32_t zero_copy_max_pages; /* continuous mode: a wave of at most this many pages skips staging and
+                                  runs in place on the working set when it is pinned, mapped memory
+                                  (default 16; 0 = always staged) */
 } ms_server_config;
 
 typedef struct ms_server_stats {

@@ -144,6 +144,7 @@ class CopyPool {
 
 struct Wave : ms::AdmittedWave {
   cudaEvent_t ev_h2d = nullptr, ev_done = nullptr;
+  bool zc = false;  // run in place on the working set (no staging copies)
 };
 
 }  // namespace
@@ -231,7 +232,10 @@ int ms_server::issue(Wave &w) {
       map.push_back({pg, k++});
     }
   }
-  const bool zc = cfg.mode == MS_SERVE_ZERO_COPY;
+  // zero-copy mode, or a small wave in continuous mode with a mapped working set
+  const bool zc = cfg.mode == MS_SERVE_ZERO_COPY || (d_host && cfg.mode == MS_SERVE_CONTINUOUS &&
+                                                     w.len <= cfg.zero_copy_max_pages);
+  w.zc = zc;
   const uint64_t tg = now_ns();
   if (zc) {  // the kernel works on the working set itself, through the host link
     for (const auto &m : map) {
@@ -280,7 +284,7 @@ void ms_server::complete(Wave &w) {
     for (uint64_t pg : slot(t).pages) map.push_back({pg, k++});
   const bool wipe = cfg.zero_staging != 0;
   const uint64_t ts = now_ns();
-  if (cfg.mode != MS_SERVE_ZERO_COPY) {
+  if (!w.zc) {
     pool->run(map.size(), [&](size_t i) {
       uint8_t *src = h_stage + (size_t)map[i].second * MS_PAGE_BYTES;
       std::memcpy(host + map[i].first * MS_PAGE_BYTES, src, MS_PAGE_BYTES);
@@ -412,6 +416,7 @@ void ms_server_config_default(ms_server_config *cfg) {
   cfg->mode = MS_SERVE_CONTINUOUS;
   cfg->max_request_pages = 4096;
   cfg->idle_spin_us = 2000;
+  cfg->zero_copy_max_pages = 16;
 }
 
 static void free_server(ms_server *s) {
@@ -461,14 +466,18 @@ int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_serv
   s->S = S;
   s->idle_spin_ns = (uint64_t)cfg.idle_spin_us * 1000ull;
   DeviceGuard g(c->device);
-  if (cfg.mode == MS_SERVE_ZERO_COPY) {
+  if (cfg.mode == MS_SERVE_ZERO_COPY || (cfg.mode == MS_SERVE_CONTINUOUS && cfg.zero_copy_max_pages)) {
     void *dp = nullptr;
     if (cudaHostGetDevicePointer(&dp, host_base, 0) != cudaSuccess || !dp) {
       cudaGetLastError();
-      delete s;
-      return MS_EINVAL;  // the working set is not pinned, mapped host memory
+      if (cfg.mode == MS_SERVE_ZERO_COPY) {
+        delete s;
+        return MS_EINVAL;  // the working set is not pinned, mapped host memory
+      }
+      s->cfg.zero_copy_max_pages = 0;  // pageable working set: every wave is staged
+    } else {
+      s->d_host = (uint64_t)dp;
     }
-    s->d_host = (uint64_t)dp;
   }
   cudaError_t e = cudaHostAlloc(&s->h_stage, (size_t)S * MS_PAGE_BYTES, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaHostAlloc(&s->h_ent, (size_t)S * sizeof(ms_page_dom), cudaHostAllocDefault);

@@ -101,6 +101,7 @@ class ms_server_config(ctypes.Structure):
         ("zero_staging", ctypes.c_uint32),
         ("max_request_pages", ctypes.c_uint32),
         ("idle_spin_us", ctypes.c_uint32),
+        ("zero_copy_max_pages", ctypes.c_uint32),
     ]
 
 
@@ -467,7 +468,7 @@ class Server:
     def __init__(self, ctx: Context, host_base, n_pages: int, *, staging_bytes: int = 0, max_wave_pages: int = 0,
                  waves_in_flight: int = 0, copy_threads: int | None = None, max_pending: int = 0,
                  mode: int = MS_SERVE_CONTINUOUS, zero_staging: bool = False, max_request_pages: int = 0,
-                 idle_spin_us: int | None = None):
+                 idle_spin_us: int | None = None, zero_copy_max_pages: int | None = None):
         cfg = ms_server_config()
         _lib.ms_server_config_default(ctypes.byref(cfg))
         if staging_bytes:
@@ -486,6 +487,8 @@ class Server:
             cfg.max_request_pages = max_request_pages
         if idle_spin_us is not None:
             cfg.idle_spin_us = idle_spin_us
+        if zero_copy_max_pages is not None:
+            cfg.zero_copy_max_pages = zero_copy_max_pages
         h = ctypes.c_void_p()
         _check(_lib.ms_server_create(ctx.handle, _ptr(host_base), n_pages, ctypes.byref(cfg), ctypes.byref(h)),
                "ms_server_create")

@@ -58,8 +58,8 @@ def test_submit_wait_matches_oracle(ms, key1):
     assert st["requests_done"] == len(reqs) and st["pages_done"] == len(touched)
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
-def test_alone_equals_mix(ms, key1, mode):
+@pytest.mark.parametrize("mode,zc_pages", [(0, None), (0, 0), (0, 4096), (1, None), (2, None)])
+def test_alone_equals_mix(ms, key1, mode, zc_pages):
     """Each request's result is identical when served alone (submit, wait, one
     at a time) and when served in a fast open-loop mix (bit-exact), and both
     equal the oracle."""
@@ -72,7 +72,7 @@ def test_alone_equals_mix(ms, key1, mode):
         with ms.Server(ctx, alone, n) as srv:
             for r in range(n_req):
                 srv.wait(srv.submit(int(ops[r]), pages[offsets[r]:offsets[r + 1]]))
-        with ms.Server(ctx, mix, n, mode=mode) as srv:
+        with ms.Server(ctx, mix, n, mode=mode, zero_copy_max_pages=zc_pages) as srv:
             lat, makespan = srv.replay(arrival, ops, offsets, pages)
             st = srv.stats()
     assert (lat >= 0).all() and makespan > 0
@@ -157,3 +157,18 @@ def test_zero_copy_needs_pinned_memory(ms, key1):
         with pytest.raises(ms.MemShieldError) as e:
             ms.Server(ctx, pageable, 16, mode=ms.MS_SERVE_ZERO_COPY)
         assert e.value.code == ms.MS_EINVAL
+
+
+def test_pageable_working_set_is_staged(ms, key1):
+    """Continuous mode over pageable memory: every wave is staged (no in-place waves)."""
+    n = 256
+    plain = synth.page_bytes(78, 0, n)
+    ws = plain.copy()
+    pages = synth.scattered_slots(79, n, 100)
+    with ms.Context(key1) as ctx, ms.Server(ctx, ws, n) as srv:
+        ts = [srv.submit(ms.MS_ENCRYPT, pages[i:i + 5]) for i in range(0, 100, 5)]
+        for t in ts:
+            srv.wait(t)
+        st = srv.stats()
+    assert np.array_equal(ws, oracle_ws(key1, plain, pages.astype(np.uint64)))
+    assert st["gather_ns"] > 0
