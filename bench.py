@@ -627,7 +627,8 @@ def serve_rows(args, rates, modes, seconds):
                 mode = mode_ids[name]
                 with ms.Server(ctx, ws, n, mode=mode, copy_threads=args.copy_threads,
                                waves_in_flight=args.waves_in_flight, idle_spin_us=args.idle_spin_us,
-                               max_wave_pages=args.max_wave_pages) as srv:
+                               max_wave_pages=args.max_wave_pages,
+                               zero_copy_max_pages=args.zero_copy_max_pages) as srv:
                     lat, makespan = srv.replay(arrival, ops, offsets, pages, timeout_ms=600000)
                     st = srv.stats()
             total = int(offsets[-1])
@@ -783,6 +784,8 @@ def main():
     ap.add_argument("--window-batches", type=lambda v: [int(x) for x in v.split(",")], default=[1, 8])
     ap.add_argument("--waves-in-flight", type=int, default=0, help="serving pipeline depth (0 = library default)")
     ap.add_argument("--max-wave-pages", type=int, default=0, help="serving wave size cap (0 = library default)")
+    ap.add_argument("--zero-copy-max-pages", type=int, default=None,
+                    help="continuous serving: waves up to this many pages run in place (default: library's)")
     ap.add_argument("--idle-spin-us", type=int, default=None, help="serving idle poll window (default: library's)")
     ap.add_argument("--serve-modes", type=lambda v: v.split(","), default=["continuous", "one_per_launch"])
     ap.add_argument("--batch-requests", type=lambda v: [int(x) for x in v.split(",")],
