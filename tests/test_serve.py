@@ -58,7 +58,7 @@ def test_submit_wait_matches_oracle(ms, key1):
     assert st["requests_done"] == len(reqs) and st["pages_done"] == len(touched)
 
 
-@pytest.mark.parametrize("mode,zc_pages", [(0, None), (0, 0), (0, 4096), (1, None), (2, None)])
+@pytest.mark.parametrize("mode,zc_pages", [(0, None), (0, 16), (0, 4096), (1, None), (2, None)])
 def test_alone_equals_mix(ms, key1, mode, zc_pages):
     """Each request's result is identical when served alone (submit, wait, one
     at a time) and when served in a fast open-loop mix (bit-exact), and both
