@@ -58,3 +58,17 @@ def test_serving_recipe():
     for r in range(0, 5000, 97):
         seg = pages[off[r]:off[r + 1]]
         assert len(np.unique(seg)) == len(seg)
+
+
+def test_window_trace_recipe():
+    n, length = 1000, 20000
+    t = synth.window_trace(7, n, length)
+    assert t.dtype == np.uint64 and len(t) == length and t.max() < n
+    assert np.array_equal(t, synth.window_trace(7, n, length))          # seeded
+    assert not np.array_equal(t, synth.window_trace(8, n, length))
+    # the scan part advances by one page per scan access
+    d = np.diff(t.astype(np.int64)) % n
+    assert (d == 1).mean() > 0.15
+    # the hot part concentrates on a few pages (Zipf 1.1)
+    counts = np.bincount(t.astype(np.int64), minlength=n)
+    assert np.sort(counts)[-10:].sum() > 0.15 * length
