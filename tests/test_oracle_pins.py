@@ -20,11 +20,16 @@ import pytest
 
 import synth
 
-crypto = pytest.importorskip("cryptography.hazmat.primitives.ciphers")
+try:
+    from cryptography.hazmat.primitives import ciphers as crypto
+except ImportError:  # only the library comparisons need it; the invariants still run
+    crypto = None
 
 
 def lib_stream(key: bytes, counter: int, nonce12: bytes, nbytes: int) -> bytes:
     """OpenSSL ChaCha20 keystream starting at ``counter``."""
+    if crypto is None:
+        pytest.skip("cryptography (OpenSSL ChaCha20) not installed")
     c = crypto.Cipher(crypto.algorithms.ChaCha20(key, struct.pack("<I", counter) + nonce12), mode=None)
     return c.encryptor().update(bytes(nbytes))
 
