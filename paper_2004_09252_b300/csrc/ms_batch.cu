@@ -2,7 +2,8 @@
 // them) are appended to a host-side queue buffer; a submit copies the buffer
 // to the device work queue and launches the persistent kernel K2 through a
 // captured CUDA graph (memset of the queue head, then K2).  Two queue buffers
-// alternate, so the host fills one while the GPU drains the other.
+// alternate, so the host fills one while the GPU drains the other, and the
+// H2D copy of a submit runs on its own stream, beside the previous K2.
 //
 // Paper counterpart (Sec. 4.4): the GPU module's workers take pages from
 // queues that many host threads fill; here one device queue per batch feeds
@@ -22,8 +23,10 @@ struct QBuf {
   uint8_t *h = nullptr;  // pinned host copy (header + items)
   uint8_t *d = nullptr;  // device work queue
   size_t n = 0;          // items queued
-  cudaEvent_t done = nullptr;
-  bool inflight = false;
+  cudaEvent_t done = nullptr;    // K2 over this buffer finished (the device copy is free again)
+  cudaEvent_t copied = nullptr;  // the H2D copy finished (the host copy is free again)
+  bool inflight = false;  // submitted, host copy possibly still being read
+  bool used = false;      // submitted at least once (done has been recorded)
   cudaGraphExec_t exec = nullptr;
   unsigned exec_key = ~0u;  // tune generation the graph was captured for
 };
@@ -35,6 +38,7 @@ struct ms_batch {
   ms_batch_config cfg{};
   QBuf buf[2];
   int cur = 0;
+  cudaStream_t copy_stream = nullptr;  // queue H2D copies, overlapping the previous K2
   std::mutex mu;
   ms_batch_stats stats{};
 };
@@ -46,15 +50,17 @@ namespace {
 int free_batch(ms_batch *b) {
   int rc = MS_OK;
   for (QBuf &q : b->buf) {
-    if (q.inflight && q.done) {
+    if (q.used && q.done) {
       int r = wait_event(b->ctx, q.done, b->ctx->cfg.timeout_ms);
       if (r != MS_OK && rc == MS_OK) rc = r;
     }
     if (q.exec) cudaGraphExecDestroy(q.exec);
     if (q.done) cudaEventDestroy(q.done);
+    if (q.copied) cudaEventDestroy(q.copied);
     if (q.h) cudaFreeHost(q.h);
     if (q.d) cudaFree(q.d);
   }
+  if (b->copy_stream) cudaStreamDestroy(b->copy_stream);
   delete b;
   return rc;
 }
@@ -118,45 +124,78 @@ cudaError_t capture(ms_batch *b, QBuf &q) {
   return e;
 }
 
-// Append one request given as ms_page (domain = the context's) or ms_page_dom.
+// The host copy of q may be rewritten once its last H2D copy has finished
+// (the kernel reading the device copy may still run).
+int host_buffer_ready(ms_ctx *c, QBuf &q) {
+  if (!q.inflight) return MS_OK;
+  DeviceGuard g(c->device);
+  const int rc = wait_event(c, q.copied, c->cfg.timeout_ms);
+  if (rc == MS_OK) q.inflight = false;
+  return rc;
+}
+
+// Copy n entries into the queue buffer at dst while checking them (address
+// non-null and 16-byte aligned).  ms_page into a per-page-domain queue takes
+// the context's domain.  Returns false on a bad entry; dst is then partly
+// written but not counted.
+template <typename E>
+bool copy_checked(const ms_batch *b, uint8_t *dst, const E *src, size_t n) {
+  constexpr bool kDom = sizeof(E) == sizeof(ms_page_dom);
+  uint64_t bad = 0;
+  if (kDom || !b->cfg.per_page_domain) {
+    E *d = reinterpret_cast<E *>(dst);
+    for (size_t i = 0; i < n; ++i) {
+      const uint64_t a = src[i].addr;
+      bad |= (uint64_t)(a == 0) | (a & 15u);
+      d[i] = src[i];
+    }
+  } else {
+    ms_page_dom *d = reinterpret_cast<ms_page_dom *>(dst);
+    const uint32_t dom = b->ctx->cfg.domain;
+    for (size_t i = 0; i < n; ++i) {
+      const uint64_t a = src[i].addr;
+      bad |= (uint64_t)(a == 0) | (a & 15u);
+      d[i] = ms_page_dom{};
+      d[i].addr = a;
+      d[i].page_id = src[i].page_id;
+      d[i].domain = dom;
+    }
+  }
+  return bad == 0;
+}
+
+// Append one request of n entries; the caller holds b->mu.
+template <typename E>
+int append_locked(ms_batch *b, int op, const E *pages, size_t n) {
+  ms_ctx *c = b->ctx;
+  if (op != MS_ENCRYPT && op != MS_DECRYPT) return MS_EINVAL;
+  if (n == 0) return MS_OK;
+  if (!pages) return MS_EINVAL;
+  QBuf &q = b->buf[b->cur];
+  if (n > b->cfg.capacity || q.n + n > b->cfg.capacity) {
+    // the entries are still checked first: a bad entry is MS_EINVAL whatever the size
+    for (size_t i = 0; i < n; ++i)
+      if (pages[i].addr == 0 || (pages[i].addr & 15u)) return MS_EINVAL;
+    return n > b->cfg.capacity ? MS_ERANGE : MS_EBUSY;  // ERANGE: can never fit; EBUSY: submit first
+  }
+  const int rc = host_buffer_ready(c, q);
+  if (rc != MS_OK) return rc;
+  if (!copy_checked(b, q.h + kHeader + item_bytes(b) * q.n, pages, n)) return MS_EINVAL;
+  q.n += n;
+  b->stats.requests += 1;
+  b->stats.pages += n;
+  return MS_OK;
+}
+
 template <typename E>
 int batch_append(ms_batch *b, int op, const E *pages, size_t n) {
   if (!b) return MS_EINVAL;
   ms_ctx *c = b->ctx;
   if (!c || !c->alive) return MS_ENOTINIT;
-  if (op != MS_ENCRYPT && op != MS_DECRYPT) return MS_EINVAL;
-  if (n == 0) return MS_OK;
-  if (!pages) return MS_EINVAL;
   constexpr bool kDom = sizeof(E) == sizeof(ms_page_dom);
   if (kDom && !b->cfg.per_page_domain) return MS_EINVAL;
-  for (size_t i = 0; i < n; ++i)
-    if (pages[i].addr == 0 || (pages[i].addr & 15u)) return MS_EINVAL;
-  if (n > b->cfg.capacity) return MS_ERANGE;  // can never fit
   std::lock_guard<std::mutex> lk(b->mu);
-  QBuf &q = b->buf[b->cur];
-  if (q.n + n > b->cfg.capacity) return MS_EBUSY;  // submit first
-  if (q.inflight) {  // the GPU may still read this buffer's previous batch
-    DeviceGuard g(c->device);
-    int rc = wait_event(c, q.done, c->cfg.timeout_ms);
-    if (rc != MS_OK) return rc;
-    q.inflight = false;
-  }
-  uint8_t *dst = q.h + kHeader + item_bytes(b) * q.n;
-  if (kDom || !b->cfg.per_page_domain) {
-    std::memcpy(dst, pages, n * sizeof(E));
-  } else {  // ms_page into a per-page-domain queue: the context's domain
-    ms_page_dom *d = reinterpret_cast<ms_page_dom *>(dst);
-    for (size_t i = 0; i < n; ++i) {
-      d[i] = ms_page_dom{};
-      d[i].addr = pages[i].addr;
-      d[i].page_id = pages[i].page_id;
-      d[i].domain = c->cfg.domain;
-    }
-  }
-  q.n += n;
-  b->stats.requests += 1;
-  b->stats.pages += n;
-  return MS_OK;
+  return append_locked(b, op, pages, n);
 }
 
 }  // namespace
@@ -186,11 +225,17 @@ int ms_batch_create(ms_ctx *c, const ms_batch_config *cfg_in, ms_batch **out) {
   b->ctx = c;
   b->cfg = cfg;
   DeviceGuard g(c->device);
+  if (cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return MS_ECUDA;
+  }
   const size_t bytes = kHeader + (cfg.per_page_domain ? sizeof(ms_page_dom) : sizeof(ms_page)) * (size_t)cfg.capacity;
   for (QBuf &q : b->buf) {
     cudaError_t e = cudaHostAlloc(&q.h, bytes, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc(&q.d, bytes);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q.copied, cudaEventDisableTiming);
     if (e != cudaSuccess) {
       free_batch(b);
       return e == cudaErrorMemoryAllocation ? MS_ENOMEM : cuda_fail(c, e);
@@ -211,10 +256,12 @@ int ms_batch_add_requests(ms_batch *b, size_t n_requests, const int *ops, const 
                           const ms_page *pages, size_t *added) {
   if (added) *added = 0;
   if (!b || (n_requests && (!ops || !offsets || !pages))) return MS_EINVAL;
-  size_t r = 0;
-  for (; r < n_requests; ++r) {
+  ms_ctx *c = b->ctx;
+  if (!c || !c->alive) return MS_ENOTINIT;
+  std::lock_guard<std::mutex> lk(b->mu);
+  for (size_t r = 0; r < n_requests; ++r) {
     if (offsets[r + 1] < offsets[r]) return MS_EINVAL;
-    const int rc = ms_batch_add(b, ops[r], pages + offsets[r], (size_t)(offsets[r + 1] - offsets[r]));
+    const int rc = append_locked(b, ops[r], pages + offsets[r], (size_t)(offsets[r + 1] - offsets[r]));
     if (rc != MS_OK) return rc;
     if (added) *added = r + 1;
   }
@@ -232,7 +279,13 @@ int ms_batch_submit(ms_batch *b) {
   DeviceGuard g(c->device);
   const uint32_t count = (uint32_t)q.n;
   std::memcpy(q.h, &count, sizeof(count));
-  cudaError_t e = cudaMemcpyAsync(q.d, q.h, kHeader + item_bytes(b) * q.n, cudaMemcpyHostToDevice, c->stream);
+  // The copy into q.d waits for the K2 that last read q.d (two submits back)
+  // and overlaps the K2 of the previous submit; this submit's K2 waits for it.
+  cudaError_t e = cudaStreamWaitEvent(b->copy_stream, q.done, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(q.d, q.h, kHeader + item_bytes(b) * q.n, cudaMemcpyHostToDevice, b->copy_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(q.copied, b->copy_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, q.copied, 0);
   if (e != cudaSuccess) return cuda_fail(c, e);
   if (b->cfg.use_graph) {
     if (!q.exec || q.exec_key != c->tune_gen.load()) {
@@ -252,6 +305,7 @@ int ms_batch_submit(ms_batch *b) {
   if (e == cudaSuccess) e = cudaEventRecord(q.done, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);
   q.inflight = true;
+  q.used = true;
   q.n = 0;
   b->stats.submits += 1;
   b->cur ^= 1;

@@ -351,11 +351,13 @@ struct QueueArgs {
 };
 
 // K2, the persistent batched kernel.  A grid sized to the resident capacity
-// of the GPU drains the work queue: each CTA claims `grab` consecutive entries
-// with one atomic on the queue head and processes them blockDim / TPP pages at a
+// of the GPU drains the work queue: each CTA claims consecutive entries with
+// one atomic on the queue head and processes them blockDim / TPP pages at a
 // time (TPP = 64 / BPT threads per page), until the head passes the count.
-// The head only grows, so every CTA leaves after at most count / grab + 1
-// claims; nothing waits.
+// Claims are guided: `grab` entries while the queue is long, then about
+// remaining / (2 * CTAs), never less than one pass, so that the CTAs run out
+// of work at nearly the same time.  The head only grows, so every CTA leaves
+// after at most count / pass + 1 claims; nothing waits.
 template <int ROUNDS, int BPT, int UNR, int POL, bool HOIST = false, bool DOM = false>
 __global__ void __launch_bounds__(512) k_queue(const QueueArgs q) {
   constexpr uint32_t TPP = 64 / BPT;
@@ -367,13 +369,23 @@ __global__ void __launch_bounds__(512) k_queue(const QueueArgs q) {
   BlockSeed s;
   load_key(q.key, s.k);
   s.n2 = q.domain;
+  __shared__ uint32_t s_take;
+  const uint32_t cap = max(q.grab, pages_per_pass);
   for (;;) {
-    if (threadIdx.x == 0) s_base = atomicAdd(q.head, q.grab);
+    if (threadIdx.x == 0) {
+      const uint32_t seen = *reinterpret_cast<volatile const uint32_t *>(q.head);
+      const uint32_t rem = seen < n ? n - seen : 0;
+      uint32_t take = rem / (2u * gridDim.x);
+      take = (take + pages_per_pass - 1) / pages_per_pass * pages_per_pass;
+      take = min(max(take, pages_per_pass), cap);
+      s_base = atomicAdd(q.head, take);
+      s_take = take;
+    }
     __syncthreads();
-    const uint32_t base = s_base;
+    const uint32_t base = s_base, take = s_take;
     __syncthreads();
     if (base >= n) break;
-    const uint32_t end = min(base + q.grab, n);
+    const uint32_t end = base + min(take, n - base);
     for (uint32_t p = base + lp; p < end; p += pages_per_pass) {
       ms_page e;
       if (DOM) {
