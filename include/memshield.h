@@ -113,7 +113,10 @@ int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg);
  * entry fails the whole call with MS_EINVAL and launches nothing.  The list is
  * copied before the call returns (the caller may reuse it at once); the work
  * is queued on the context's stream and completes asynchronously: ms_sync()
- * waits for it.
+ * waits for it.  Up to 1024 entries (512 with per-page domains) travel in the
+ * kernel's parameters: one launch, no copy.  Longer lists, or any list on a
+ * context whose shape the caller set, go through pinned staging slots of
+ * list_capacity entries and one host-to-device copy per slot.
  */
 int ms_encrypt_pages(ms_ctx *ctx, const ms_page *pages, size_t n);
 int ms_decrypt_pages(ms_ctx *ctx, const ms_page *pages, size_t n);
@@ -405,7 +408,12 @@ int ms_server_wait(ms_server *srv, uint64_t ticket, uint32_t timeout_ms);
  * latency_s[r] is its completion time minus that scheduled arrival (so
  * queueing delay counts: no coordinated omission).  *makespan_s receives the
  * time from the start to the last completion.  Waits at most timeout_ms
- * after the last arrival for completions.
+ * after the last arrival for completions.  Every request is checked before
+ * the first is submitted (MS_EINVAL: empty request, bad op, page index out
+ * of range or repeated within a request; MS_ERANGE: more than
+ * max_request_pages).  On an error return after submission started,
+ * requests still outstanding run to completion but no longer write to
+ * latency_s, so the caller may free it at once.
  */
 int ms_server_replay(ms_server *srv, size_t n_requests, const double *arrival_s, const int *ops,
                      const uint32_t *domains, const uint64_t *offsets, const uint64_t *page_index,

@@ -26,7 +26,6 @@ struct QBuf {
   cudaEvent_t done = nullptr;    // K2 over this buffer finished (the device copy is free again)
   cudaEvent_t copied = nullptr;  // the H2D copy finished (the host copy is free again)
   bool inflight = false;  // submitted, host copy possibly still being read
-  bool used = false;      // submitted at least once (done has been recorded)
   cudaGraphExec_t exec = nullptr;
   unsigned exec_key = ~0u;  // tune generation the graph was captured for
 };
@@ -50,10 +49,14 @@ namespace {
 int free_batch(ms_batch *b) {
   int rc = MS_OK;
   for (QBuf &q : b->buf) {
-    if (q.used && q.done) {
-      int r = wait_event(b->ctx, q.done, b->ctx->cfg.timeout_ms);
-      if (r != MS_OK && rc == MS_OK) rc = r;
-    }
+    // An event never recorded counts as complete, so both waits are safe on
+    // buffers that were never submitted; a copy enqueued by a submit that
+    // failed later is waited for too.
+    for (cudaEvent_t ev : {q.copied, q.done})
+      if (ev) {
+        int r = wait_event(b->ctx, ev, b->ctx->cfg.timeout_ms);
+        if (r != MS_OK && rc == MS_OK) rc = r;
+      }
     if (q.exec) cudaGraphExecDestroy(q.exec);
     if (q.done) cudaEventDestroy(q.done);
     if (q.copied) cudaEventDestroy(q.copied);
@@ -305,7 +308,6 @@ int ms_batch_submit(ms_batch *b) {
   if (e == cudaSuccess) e = cudaEventRecord(q.done, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);
   q.inflight = true;
-  q.used = true;
   q.n = 0;
   b->stats.submits += 1;
   b->cur ^= 1;

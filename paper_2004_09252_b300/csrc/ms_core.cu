@@ -87,6 +87,12 @@ int submit_list_host(ms_ctx *c, const E *pages, size_t n) {
   }
   std::lock_guard<std::mutex> lk(c->mu);
   DeviceGuard g(c->device);
+  // A short list goes in the kernel parameters: one launch, no copies.  A
+  // shape the caller chose is kept, so such contexts take the staged path.
+  if (n <= inline_max_pages<E>() && !c->shape_explicit) {
+    const cudaError_t e = launch_pages_inline(c, pages, n, c->stream);
+    return e == cudaSuccess ? MS_OK : cuda_fail(c, e);
+  }
   const size_t cap = c->cfg.list_capacity;  // slots hold cap entries of the larger layout
   for (size_t off = 0; off < n; off += cap) {
     const size_t cnt = std::min(cap, n - off);
@@ -122,6 +128,7 @@ int submit_list_dev(ms_ctx *c, const E *d_pages, size_t n) {
   PageArgs a = make_args(c);
   set_list<E>(a, d_pages);
   a.n_pages = n;
+  c->status_dirty = true;  // set even if the launch fails: a read costs only time
   cudaError_t e = launch_pages(c, a, c->stream);
   return e == cudaSuccess ? MS_OK : cuda_fail(c, e);
 }
@@ -328,18 +335,26 @@ int ms_sync_for(ms_ctx *c, uint32_t timeout_ms) {
     c->status_pending = false;
     c->status_acc |= *(volatile unsigned int *)c->h_status;
   }
-  // Phase 1: wait for the submitted work; a timeout here leaves nothing queued.
-  cudaError_t e = cudaEventRecord(c->sync_ev, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e);
-  int rc = wait_event(c, c->sync_ev, timeout_ms);
-  if (rc != MS_OK) return rc;
-  // Phase 2: read and clear the device status word.
-  e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream);
+  if (!c->status_dirty) {
+    // Nothing since the last read can have set a status bit: wait for the work.
+    cudaError_t e = cudaEventRecord(c->sync_ev, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    const int rc = wait_event(c, c->sync_ev, timeout_ms);
+    if (rc != MS_OK) return rc;
+    const unsigned st = c->status_acc;
+    c->status_acc = 0;
+    return (st & kStatusBadEntry) ? MS_EINVAL : MS_OK;
+  }
+  // Queue the read and clear of the device status word behind the submitted
+  // work and wait once (one round trip).  On a timeout the read stays
+  // pending and the next call collects it first (above).
+  cudaError_t e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream);
   if (e == cudaSuccess) e = cudaEventRecord(c->status_ev, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);
+  c->status_dirty = false;  // the queued read covers every launch before it
   c->status_pending = true;
-  rc = wait_event(c, c->status_ev, timeout_ms > 1000 ? timeout_ms : 1000);
+  int rc = wait_event(c, c->status_ev, timeout_ms);
   if (rc != MS_OK) return rc;
   c->status_pending = false;
   const unsigned st = *(volatile unsigned int *)c->h_status | c->status_acc;

@@ -57,6 +57,9 @@ struct ms_ctx {
   cudaEvent_t status_ev = nullptr;   // the status-word read of ms_sync
   bool status_pending = false;       // that read was queued but not yet collected
   unsigned status_acc = 0;           // status bits collected by a call that then timed out
+  bool status_dirty = false;         // a device-list launch since the last status read: only
+                                     // those can set a status bit (every other entry is checked
+                                     // on the host or built by the library)
   ms::Tune tune;
   bool shape_explicit = false;  // set by the caller (config, ms_set_shape, a loaded table): never adapted
   ms::QTune qtune;
@@ -104,6 +107,12 @@ cudaError_t launch_pages(const ms_ctx *c, const PageArgs &a, cudaStream_t s);
 cudaError_t launch_pages_shape(const PageArgs &a, int rounds, const Tune &t, bool range,
                                cudaStream_t s);
 bool shape_available(int rounds, const Tune &t);
+// K1 with a short host entry list carried in the kernel parameters (no
+// staging copy); n <= inline_max_pages<E>() (1024 ms_page, 512 ms_page_dom).
+template <typename E>
+size_t inline_max_pages();
+template <typename E>
+cudaError_t launch_pages_inline(const ms_ctx *c, const E *pages, size_t n, cudaStream_t s);
 int k1_shape_count();
 void k1_shape(int i, int *rounds, Tune *t);
 

@@ -214,7 +214,10 @@ int ms_server::issue(Wave &w) {
   if (ev_pool.empty()) {
     cudaEvent_t a, b;
     if (cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess) return MS_ECUDA;
-    if (cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) return MS_ECUDA;
+    if (cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return MS_ECUDA;
+    }
     ev_pool.push_back({a, b});
   }
   w.ev_h2d = ev_pool.back().first;
@@ -295,14 +298,20 @@ void ms_server::complete(Wave &w) {
   st_scatter_ns.fetch_add(t - ts);
   uint64_t pages = 0;
   {
-    std::lock_guard<std::mutex> lk(qmu);  // the admission state is shared with form_wave
+    // qmu guards the admission state (shared with form_wave) and lat_out
+    // (a replay that gives up detaches its outstanding requests under it)
+    std::lock_guard<std::mutex> lk(qmu);
     adm->release(w, [&](uint64_t t) -> const std::vector<uint64_t> & { return slot(t).pages; });
+    for (uint64_t tk : w.tickets) {
+      Req &r = slot(tk);
+      if (r.lat_out) *r.lat_out = (double)((int64_t)(t - r.t_sched_ns)) * 1e-9;
+      r.lat_out = nullptr;
+    }
   }
   for (uint64_t tk : w.tickets) {
     Req &r = slot(tk);
     pages += r.pages.size();
     r.t_done_ns.store(t);
-    if (r.lat_out) *r.lat_out = (double)((int64_t)(t - r.t_sched_ns)) * 1e-9;
     r.state.store(kDone, std::memory_order_release);
   }
   ev_pool.push_back({w.ev_h2d, w.ev_done});
@@ -588,7 +597,19 @@ int ms_server_replay(ms_server *s, size_t n, const double *arrival_s, const int 
                      const uint64_t *offsets, const uint64_t *page_index, double *latency_s, double *makespan_s,
                      uint32_t timeout_ms) {
   if (!s || (n && (!arrival_s || !ops || !offsets || !page_index || !latency_s))) return MS_EINVAL;
-  for (size_t r = 0; r < n; ++r) latency_s[r] = -1.0;
+  // every request is checked before the first one is submitted
+  for (size_t r = 0; r < n; ++r) {
+    if (offsets[r + 1] <= offsets[r] || (ops[r] != MS_ENCRYPT && ops[r] != MS_DECRYPT)) return MS_EINVAL;
+    if (offsets[r + 1] - offsets[r] > s->cfg.max_request_pages) return MS_ERANGE;
+    for (uint64_t k = offsets[r]; k < offsets[r + 1]; ++k)
+      if (page_index[k] >= s->n_pages) return MS_EINVAL;
+    if (offsets[r + 1] - offsets[r] > 1) {  // distinct pages within a request
+      std::vector<uint64_t> tmp(page_index + offsets[r], page_index + offsets[r + 1]);
+      std::sort(tmp.begin(), tmp.end());
+      if (std::adjacent_find(tmp.begin(), tmp.end()) != tmp.end()) return MS_EINVAL;
+    }
+    latency_s[r] = -1.0;
+  }
   // precise pacing: short timer slack for this thread while replaying
   const int old_slack = prctl(PR_GET_TIMERSLACK, 0, 0, 0, 0);
   prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);
@@ -600,6 +621,17 @@ int ms_server_replay(ms_server *s, size_t n, const double *arrival_s, const int 
   } restore{old_slack};
   const uint64_t t0 = now_ns() + 1000000ull;  // start 1 ms from now
   std::vector<uint64_t> tickets(n);
+  size_t issued = 0;
+  // On an early return the requests still queued or running must stop
+  // pointing into latency_s, which the caller may free once this returns.
+  auto detach = [&](int rc) {
+    std::lock_guard<std::mutex> lk(s->qmu);
+    for (size_t r = 0; r < issued; ++r) {
+      Req &q = s->slot(tickets[r]);
+      if (q.ticket.load() == tickets[r]) q.lat_out = nullptr;
+    }
+    return rc;
+  };
   for (size_t r = 0; r < n; ++r) {
     const uint64_t target = t0 + (uint64_t)(arrival_s[r] * 1e9);
     for (;;) {
@@ -613,9 +645,12 @@ int ms_server_replay(ms_server *s, size_t n, const double *arrival_s, const int 
       const uint32_t dom = domains ? domains[r] : s->ctx->cfg.domain;
       int rc = submit_internal(s, ops[r], dom, page_index + offsets[r], (uint32_t)n_pg, &tickets[r], target,
                                &latency_s[r]);
-      if (rc == MS_OK) break;
-      if (rc != MS_EBUSY) return rc;
-      if (now_ns() > spin_limit) return MS_ETIMEDOUT;
+      if (rc == MS_OK) {
+        issued = r + 1;
+        break;
+      }
+      if (rc != MS_EBUSY) return detach(rc);
+      if (now_ns() > spin_limit) return detach(MS_ETIMEDOUT);
       nap_ns(5000);
     }
   }
@@ -624,9 +659,9 @@ int ms_server_replay(ms_server *s, size_t n, const double *arrival_s, const int 
   for (size_t r = 0; r < n; ++r) {
     for (;;) {
       int p = ms_server_poll(s, tickets[r]);
-      if (p < 0) return p;
+      if (p < 0) return detach(p);
       if (p == 1) break;
-      if (now_ns() > deadline) return MS_ETIMEDOUT;
+      if (now_ns() > deadline) return detach(MS_ETIMEDOUT);
       nap_ns(5000);
     }
   }
@@ -660,11 +695,24 @@ int ms_server_destroy(ms_server *s) {
   if (s->th.joinable()) s->th.join();
   int rc = s->error.load();
   DeviceGuard g(s->ctx->device);
-  // everything the server issued must be finished before its buffers go
+  // everything the server issued must be finished before its buffers go:
+  // the waves still listed, and any copy of a wave whose issue failed midway
   for (Wave &w : s->inflight) {
+    if (!w.ev_done) continue;  // its issue failed before it had events
     int r = wait_event(s->ctx, w.ev_done, s->ctx->cfg.timeout_ms);
     if (r != MS_OK) return r;  // still running on the GPU: leave the buffers allocated
   }
+  for (cudaStream_t st : {s->s_in, s->s_work[0], s->s_work[1]}) {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return cuda_fail(s->ctx, cudaGetLastError());
+    cudaError_t e = cudaEventRecord(ev, st);
+    int r = e == cudaSuccess ? wait_event(s->ctx, ev, s->ctx->cfg.timeout_ms) : cuda_fail(s->ctx, e);
+    cudaEventDestroy(ev);
+    if (r != MS_OK) return r;
+  }
+  for (Wave &w : s->inflight)
+    if (w.ev_done) s->ev_pool.push_back({w.ev_h2d, w.ev_done});
+  s->inflight.clear();
   ms_ctx *c = s->ctx;
   free_server(s);
   c->children.fetch_sub(1);

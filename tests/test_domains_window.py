@@ -28,6 +28,23 @@ def oracle_by_domain(key, plain, slots, ids, domains):
     return out
 
 
+@pytest.mark.parametrize("n", [1, 16, 129, 512, 513])
+def test_per_page_domains_short_host_lists(ms, key1, n):
+    """Host lists with a domain per entry: up to 512 travel in the kernel's
+    parameters, 513 takes the staged path."""
+    n_slots = n + 11
+    plain = synth.page_bytes(95, 0, n_slots)
+    slots = synth.scattered_slots(96, n_slots, n).astype(np.uint64)
+    ids = synth.splitmix64(97, 0, n).astype(np.uint64)
+    doms = (synth.splitmix64(98, 0, n) % np.uint64(7)).astype(np.uint32) * np.uint32(0x10001)
+    want = oracle_by_domain(key1, plain, slots, ids, doms)
+    with ms.Context(key1, stream=torch.cuda.current_stream(), domain=999) as ctx:
+        d = torch.from_numpy(plain).cuda()
+        ctx.crypt_pages_dom(ms.pages_dom_array(d.data_ptr() + PAGE * slots, ids, doms))
+        ctx.sync_checked()
+        assert np.array_equal(d.cpu().numpy(), want)
+
+
 @pytest.mark.parametrize("shape", [None, (1, 256, 10, 1, 0), (4, 128, 10, 1, 0), (2, 512, 10, 0, 1)])
 def test_per_page_domains_host_and_device_lists(ms, key1, shape):
     n_slots, n = 300, 257

@@ -31,9 +31,9 @@ def test_inject_rejects_bad_arguments(ms):
     ms.inject_fault(0)
 
 
-@pytest.mark.parametrize("site", ["launch", "copy"])
-def test_one_launch_form_recovers(ms, key1, site):
-    n = 32
+@pytest.mark.parametrize("site,n", [("launch", 32), ("launch", 2000), ("copy", 2000)])
+def test_one_launch_form_recovers(ms, key1, site, n):
+    # 32 entries travel in the kernel parameters; 2000 take the staged copy
     plain = synth.page_bytes(120, 0, n)
     d = torch.from_numpy(plain).cuda()
     ids = np.arange(n, dtype=np.uint64)
@@ -117,3 +117,45 @@ def test_server_failure_fails_requests_cleanly(ms, key1):
     want = plain.copy()
     oracle.crypt_pages(key1, want, np.array([7, 8]), np.array([7, 8]))
     assert np.array_equal(h.numpy(), want)
+
+
+def test_server_replay_failure_returns_cleanly(ms, key1):
+    """A wave that fails in the middle of an open-loop replay ends the replay with
+    MS_ECUDA; requests still outstanding no longer write to the caller's latency
+    array, and the context serves a new server afterwards."""
+    n = 512
+    plain = synth.page_bytes(125, 0, n)
+    h = torch.from_numpy(plain.copy()).pin_memory()
+    n_req = 200
+    arrival = np.linspace(0.0, 0.004, n_req)
+    ops = np.full(n_req, ms.MS_ENCRYPT, dtype=np.int32)
+    offsets = np.arange(n_req + 1, dtype=np.uint64)
+    pages = np.arange(n_req, dtype=np.uint64)
+    with ms.Context(key1) as ctx:
+        srv = ms.Server(ctx, h, n, mode=ms.MS_SERVE_ONE_PER_LAUNCH)
+        ms.inject_fault(ms.MS_FAULT_SERVER, 20, ERR)        # the 21st wave fails
+        with pytest.raises(ms.MemShieldError) as e:
+            srv.replay(arrival, ops, offsets, pages, timeout_ms=5000)
+        assert e.value.code == ms.MS_ECUDA
+        srv.destroy()
+        with ms.Server(ctx, h, n) as srv2:
+            srv2.wait(srv2.submit(ms.MS_ENCRYPT, [n - 1]))
+    last = slice((n - 1) * PAGE, n * PAGE)
+    want = oracle_expected(key1, plain[last], np.array([0]), np.array([n - 1]))
+    assert np.array_equal(h.numpy()[last], want)
+
+
+def test_server_replay_checks_every_request_first(ms, key1):
+    n = 64
+    h = torch.zeros(n * PAGE, dtype=torch.uint8).pin_memory()
+    arrival = np.zeros(3)
+    ops = np.full(3, ms.MS_ENCRYPT, dtype=np.int32)
+    with ms.Context(key1) as ctx, ms.Server(ctx, h, n) as srv:
+        for offsets, pages in (([0, 1, 2, 3], [1, 2, n]),       # page out of range in the last request
+                               ([0, 1, 1, 2], [1, 2]),          # empty request
+                               ([0, 1, 3, 4], [1, 2, 2, 3])):   # page repeated within a request
+            with pytest.raises(ms.MemShieldError) as e:
+                srv.replay(arrival, ops, np.array(offsets, dtype=np.uint64), np.array(pages, dtype=np.uint64))
+            assert e.value.code == ms.MS_EINVAL
+        assert srv.stats()["requests_done"] == 0                 # nothing was submitted
+    assert not h.numpy().any()

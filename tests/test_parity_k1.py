@@ -184,8 +184,9 @@ def test_duplicate_check(ms, key1):
 
 
 def test_list_longer_than_staging_slot(ms, key1):
-    """A host list longer than one staging slot is cut into several launches."""
-    n = 300
+    """A host list longer than one staging slot (and than the parameter-space
+    limit of 1024 entries) is cut into several staged launches."""
+    n = 1500
     plain = synth.page_bytes(15, 0, n)
     d = dev(plain)
     ids = np.arange(n, dtype=np.uint64)
@@ -194,6 +195,46 @@ def test_list_longer_than_staging_slot(ms, key1):
             ctx.encrypt_pages(ms.pages_array(d.data_ptr() + PAGE * ids, ids))
         ctx.sync_checked()
     assert np.array_equal(d.cpu().numpy(), oracle_expected(key1, plain, ids, ids))
+
+
+@pytest.mark.parametrize("rounds", [20, 12, 8])
+@pytest.mark.parametrize("n", [1, 16, 17, 128, 129, 1000, 1024, 1025])
+def test_short_host_lists_in_kernel_parameters(ms, key1, n, rounds):
+    """Host lists of up to 1024 entries travel in the kernel's parameters (16-,
+    128- and 1024-entry blocks); 1025 takes the staged path.  Scattered slots,
+    full 64-bit ids, a non-zero domain."""
+    n_slots = n + 37
+    plain = synth.page_bytes(150 + n, 0, n_slots)
+    d = dev(plain)
+    slots = synth.scattered_slots(151 + n, n_slots, n)
+    ids = synth.splitmix64(152 + n, 0, n).astype(np.uint64)
+    with make_ctx(ms, key1, rounds=rounds, domain=0x5A5A5A5A) as ctx:
+        ctx.encrypt_pages(ms.pages_array(d.data_ptr() + PAGE * slots.astype(np.uint64), ids))
+        ctx.sync_checked()
+        want = oracle_expected(key1, plain, slots, ids, domain=0x5A5A5A5A, rounds=rounds)
+        assert np.array_equal(d.cpu().numpy(), want)
+        ctx.decrypt_pages(ms.pages_array(d.data_ptr() + PAGE * slots.astype(np.uint64), ids))
+        ctx.sync_checked()
+        assert np.array_equal(d.cpu().numpy(), plain)
+
+
+def test_short_host_lists_back_to_back(ms, key1):
+    """Many short launches queued without a wait: every parameter block is the
+    caller's list at the time of the call, even though the caller reuses its
+    array at once."""
+    n_slots = 4096
+    plain = synth.page_bytes(160, 0, n_slots)
+    d = dev(plain)
+    lst = ms.pages_array(np.zeros(8, np.uint64), np.zeros(8, np.uint64))
+    with make_ctx(ms, key1) as ctx:
+        for r in range(n_slots // 8):
+            sl = np.arange(8 * r, 8 * r + 8, dtype=np.uint64)
+            lst["addr"] = d.data_ptr() + PAGE * sl
+            lst["page_id"] = sl
+            ctx.encrypt_pages(lst)
+        ctx.sync_checked()
+    all_ = np.arange(n_slots)
+    assert np.array_equal(d.cpu().numpy(), oracle_expected(key1, plain, all_, all_))
 
 
 @pytest.mark.slow
