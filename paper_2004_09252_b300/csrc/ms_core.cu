@@ -22,6 +22,14 @@ int cuda_fail(ms_ctx *c, cudaError_t e) {
   return MS_ECUDA;
 }
 
+// Moves the device status word to the mapped host word and clears it: one
+// launch where a copy and a memset would be two operations on the stream.
+__global__ void k_status_take(unsigned int *d_status, unsigned int *h_status) {
+  const unsigned int v = *d_status;
+  *d_status = 0;
+  *(volatile unsigned int *)h_status = v;
+}
+
 namespace {
 std::atomic<int> g_fault_mask{0};
 std::atomic<int> g_fault_countdown{0};
@@ -239,7 +247,8 @@ int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg_in) {
   MS_TRY(cudaEventCreateWithFlags(&c->status_ev, cudaEventDisableTiming));
   MS_TRY(cudaMalloc(&c->d_status, sizeof(unsigned int)));
   MS_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream));
-  MS_TRY(cudaHostAlloc(&c->h_status, sizeof(unsigned int), cudaHostAllocDefault));
+  MS_TRY(cudaHostAlloc(&c->h_status, sizeof(unsigned int), cudaHostAllocMapped));
+  MS_TRY(cudaHostGetDevicePointer((void **)&c->h_status_dev, c->h_status, 0));
   for (auto &s : c->slots) {
     MS_TRY(cudaHostAlloc(&s.h, sizeof(ms_page_dom) * cfg.list_capacity, cudaHostAllocDefault));
     MS_TRY(cudaMalloc(&s.d, sizeof(ms_page_dom) * cfg.list_capacity));
@@ -348,8 +357,8 @@ int ms_sync_for(ms_ctx *c, uint32_t timeout_ms) {
   // Queue the read and clear of the device status word behind the submitted
   // work and wait once (one round trip).  On a timeout the read stays
   // pending and the next call collects it first (above).
-  cudaError_t e = cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned int), c->stream);
+  k_status_take<<<1, 1, 0, c->stream>>>(c->d_status, c->h_status_dev);
+  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaEventRecord(c->status_ev, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);
   c->status_dirty = false;  // the queued read covers every launch before it

@@ -52,7 +52,8 @@ struct ms_ctx {
   int sm_count = 0;
   uint4 *d_key = nullptr;          // the 32-byte key, device memory only
   unsigned int *d_status = nullptr;
-  unsigned int *h_status = nullptr;  // pinned landing word for ms_sync
+  unsigned int *h_status = nullptr;  // pinned, mapped landing word for ms_sync
+  unsigned int *h_status_dev = nullptr;  // its device address
   cudaEvent_t sync_ev = nullptr;
   cudaEvent_t status_ev = nullptr;   // the status-word read of ms_sync
   bool status_pending = false;       // that read was queued but not yet collected
