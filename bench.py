@@ -721,38 +721,48 @@ def run_window(args):
     synth.fill_pages(ws.data_ptr(), 6, 0, n)
     ctx = ms.Context(key)
     rows = []
-    with ms.Server(ctx, ws, n) as srv:
+    srv = ms.Server(ctx, ws, n)
+    res = ms.Resident(ctx, workers=args.resident_workers) if "resident" in args.window_backends else None
+    try:
         for c in range(max_clients):           # client pages start encrypted with the client's PID
             for p0 in range(c * per, (c + 1) * per, 4096):
                 srv.wait(srv.submit(ms.MS_ENCRYPT, np.arange(p0, min(p0 + 4096, (c + 1) * per)), domain=1000 + c),
                          20000)
         traces = [synth.window_trace(200 + c, per, args.window_trace) for c in range(max_clients)]
         state = {}
-        for n_cl in args.window_clients:
-            for wnd in args.window_sizes:
-                for batch in args.window_batches:
-                    if batch > wnd + 1:
-                        continue
-                    # clients resume from where the previous run left their windows: re-encrypt them first
-                    for c, win in state.items():
-                        if win:
-                            srv.wait(srv.submit(ms.MS_ENCRYPT, np.array(win), domain=1000 + c), 20000)
-                    state = {}
-                    cl = [(1000 + c, c * per, per, traces[c]) for c in range(n_cl)]
-                    t0 = time.perf_counter()
-                    st, wins = srv.run_window_clients(wnd, batch, cl, timeout_ms=20000)
-                    el = time.perf_counter() - t0
-                    state = {c: wins[c] for c in range(n_cl)}
-                    faults = sum(x["faults"] for x in st)
-                    rows.append({"clients": n_cl, "window_pages": wnd, "evict_batch": batch,
-                                 "accesses": sum(x["accesses"] for x in st), "faults": faults,
-                                 "evictions": sum(x["evictions"] for x in st),
-                                 "evict_requests": sum(x["evict_requests"] for x in st),
-                                 "faults_per_s": round(faults / el, 1),
-                                 "fault_p50_us": round(float(np.mean([x["fault_p50_us"] for x in st])), 1),
-                                 "fault_p99_us": round(float(max(x["fault_p99_us"] for x in st)), 1),
-                                 "client_s_max": round(max(x["elapsed_s"] for x in st), 3)})
-                    print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        for backend in args.window_backends:
+            for n_cl in args.window_clients:
+                for wnd in args.window_sizes:
+                    for batch in args.window_batches:
+                        if batch > wnd + 1:
+                            continue
+                        # clients resume from where the previous run left their windows: re-encrypt them first
+                        for c, win in state.items():
+                            if win:
+                                srv.wait(srv.submit(ms.MS_ENCRYPT, np.array(win), domain=1000 + c), 20000)
+                        state = {}
+                        cl = [(1000 + c, c * per, per, traces[c]) for c in range(n_cl)]
+                        t0 = time.perf_counter()
+                        if backend == "resident":
+                            st, wins = res.run_window_clients(ws, n, wnd, batch, cl, timeout_ms=20000)
+                        else:
+                            st, wins = srv.run_window_clients(wnd, batch, cl, timeout_ms=20000)
+                        el = time.perf_counter() - t0
+                        state = {c: wins[c] for c in range(n_cl)}
+                        faults = sum(x["faults"] for x in st)
+                        rows.append({"backend": backend, "clients": n_cl, "window_pages": wnd, "evict_batch": batch,
+                                     "accesses": sum(x["accesses"] for x in st), "faults": faults,
+                                     "evictions": sum(x["evictions"] for x in st),
+                                     "evict_requests": sum(x["evict_requests"] for x in st),
+                                     "faults_per_s": round(faults / el, 1),
+                                     "fault_p50_us": round(float(np.mean([x["fault_p50_us"] for x in st])), 1),
+                                     "fault_p99_us": round(float(max(x["fault_p99_us"] for x in st)), 1),
+                                     "client_s_max": round(max(x["elapsed_s"] for x in st), 3)})
+                        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    finally:
+        if res is not None:
+            res.destroy()
+        srv.destroy()
     ctx.shutdown()
     print(json.dumps({
         "metric": "sliding-window fault service (faults/s, fault latency)", "unit": "faults/s",
@@ -839,6 +849,8 @@ def main():
     ap.add_argument("--window-clients", type=lambda v: [int(x) for x in v.split(",")], default=[1, 2, 4])
     ap.add_argument("--window-sizes", type=lambda v: [int(x) for x in v.split(",")], default=[4, 8, 16, 32])
     ap.add_argument("--window-batches", type=lambda v: [int(x) for x in v.split(",")], default=[1, 8])
+    ap.add_argument("--window-backends", type=lambda v: v.split(","), default=["server", "resident"],
+                    help="serve the window clients through the staged server and/or resident workers")
     ap.add_argument("--waves-in-flight", type=int, default=0, help="serving pipeline depth (0 = library default)")
     ap.add_argument("--max-wave-pages", type=int, default=0, help="serving wave size cap (0 = library default)")
     ap.add_argument("--zero-copy-max-pages", type=int, default=None,

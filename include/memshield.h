@@ -526,6 +526,18 @@ int ms_resident_destroy(ms_resident *res);
 int ms_resident_replay(ms_resident *res, void *host_base, uint64_t n_pages, size_t n_requests,
                        const double *arrival_s, const uint32_t *domains, const uint64_t *offsets,
                        const uint64_t *page_index, double *latency_s, double *makespan_s, uint32_t timeout_ms);
+/*
+ * The sliding-window clients of ms_window_run, served by resident workers:
+ * every fault is one resident request (decrypt, waited for) and every
+ * eviction one request per page (encrypt, not waited for).  The working set
+ * (n_pages pages at host_base, page index = page id) must be pinned, mapped
+ * host memory; the workers read and write it in place.  A fault on a page
+ * whose eviction is still running waits for that eviction first, so no page
+ * is ever in flight twice.  Client ranges must lie inside the working set.
+ */
+int ms_window_run_resident(ms_resident *res, void *host_base, uint64_t n_pages, const ms_window_config *cfg,
+                           const ms_window_client *clients, size_t n_clients, ms_window_stats *stats_out,
+                           uint64_t *final_window_out, uint32_t timeout_ms);
 
 /*
  * Allocation-free variant of ms_encrypt_pages / ms_decrypt_pages.  The paper

@@ -1,5 +1,7 @@
 // Sliding-window client driver: produces the paper's fault / eviction stream
-// (Sec. 4.3) from page-access traces and serves it through an ms_server.
+// (Sec. 4.3) from page-access traces and serves it through an ms_server
+// (staged waves) or through resident workers (one page per request, in place
+// on the pinned working set, as the paper's GPU module does).
 //
 // Each client owns a range of working-set pages, all encrypted at the start,
 // and a FIFO window of pages in clear.  An access to a page outside the
@@ -29,11 +31,99 @@ struct ClientRun {
   ms_window_stats st{};
   std::vector<double> lat_us;
   std::vector<uint64_t> final_window;
-  std::vector<uint64_t> evict_tickets;
   int rc = MS_OK;
 };
 
-void run_client(ms_server *srv, const ms_window_config &cfg, ClientRun &cr, uint32_t timeout_ms) {
+// Where a client's requests go.  Fault: decrypt one page and wait for it.
+// Evict: encrypt pages without waiting.  Drain: wait for every eviction.
+struct ServerBackend {
+  ms_server *srv;
+  uint32_t timeout_ms;
+  std::vector<uint64_t> evict_tickets;
+  int fault(uint32_t domain, uint64_t pg) {
+    uint64_t ticket;
+    int rc;
+    for (;;) {
+      rc = ms_server_submit_dom(srv, MS_DECRYPT, domain, &pg, 1, &ticket);
+      if (rc != MS_EBUSY) break;
+      std::this_thread::yield();
+    }
+    // an eviction of this page still in flight is waited for by the server's in-flight rule
+    return rc == MS_OK ? ms_server_wait(srv, ticket, timeout_ms) : rc;
+  }
+  int evict(uint32_t domain, const uint64_t *pages, size_t k) {
+    uint64_t ticket;
+    int rc;
+    for (;;) {
+      rc = ms_server_submit_dom(srv, MS_ENCRYPT, domain, pages, (uint32_t)k, &ticket);
+      if (rc != MS_EBUSY) break;
+      std::this_thread::yield();
+    }
+    if (rc == MS_OK) evict_tickets.push_back(ticket);
+    return rc;
+  }
+  int drain() {
+    for (uint64_t t : evict_tickets) {
+      const int rc = ms_server_wait(srv, t, timeout_ms);
+      if (rc != MS_OK) return rc;
+    }
+    return MS_OK;
+  }
+};
+
+struct ResidentBackend {
+  ms_resident *res;
+  uint64_t dbase;       // device address of the working set
+  uint64_t first_page;  // the client's range, for last_ticket
+  uint32_t timeout_ms;
+  std::vector<uint64_t> last_ticket;  // per client page: its latest request, ~0 = none
+  std::vector<uint64_t> evict_tickets;
+  int submit(uint32_t domain, uint64_t pg, uint64_t *ticket) {
+    ms_page_dom e{};
+    e.addr = dbase + pg * MS_PAGE_BYTES;
+    e.page_id = pg;
+    e.domain = domain;
+    const auto limit = clk::now() + std::chrono::milliseconds(timeout_ms);
+    for (;;) {
+      const int rc = ms_resident_submit(res, &e, ticket);
+      if (rc != MS_EBUSY) return rc;
+      if (clk::now() > limit) return MS_ETIMEDOUT;
+      std::this_thread::yield();
+    }
+  }
+  int fault(uint32_t domain, uint64_t pg) {
+    uint64_t &last = last_ticket[pg - first_page];
+    if (last != ~0ull) {  // its eviction may still be running: a page is never in flight twice
+      const int rc = ms_resident_wait(res, last, timeout_ms);
+      if (rc != MS_OK) return rc;
+    }
+    uint64_t ticket;
+    int rc = submit(domain, pg, &ticket);
+    if (rc == MS_OK) rc = ms_resident_wait(res, ticket, timeout_ms);
+    last = ~0ull;
+    return rc;
+  }
+  int evict(uint32_t domain, const uint64_t *pages, size_t k) {
+    for (size_t i = 0; i < k; ++i) {
+      uint64_t ticket;
+      const int rc = submit(domain, pages[i], &ticket);
+      if (rc != MS_OK) return rc;
+      last_ticket[pages[i] - first_page] = ticket;
+      evict_tickets.push_back(ticket);
+    }
+    return MS_OK;
+  }
+  int drain() {
+    for (uint64_t t : evict_tickets) {
+      const int rc = ms_resident_wait(res, t, timeout_ms);
+      if (rc != MS_OK) return rc;
+    }
+    return MS_OK;
+  }
+};
+
+template <typename Backend>
+void run_client(Backend &be, const ms_window_config &cfg, ClientRun &cr) {
   const ms_window_client &cl = *cr.cl;
   std::deque<uint64_t> window;  // working-set page indices in clear, oldest first
   std::unordered_set<uint64_t> in_window;
@@ -53,14 +143,7 @@ void run_client(ms_server *srv, const ms_window_config &cfg, ClientRun &cr, uint
     }
     // fault: decrypt the page and wait for it
     const auto f0 = clk::now();
-    uint64_t ticket;
-    int rc;
-    for (;;) {
-      rc = ms_server_submit_dom(srv, MS_DECRYPT, cl.domain, &pg, 1, &ticket);
-      if (rc != MS_EBUSY) break;
-      std::this_thread::yield();
-    }
-    if (rc == MS_OK) rc = ms_server_wait(srv, ticket, timeout_ms);
+    int rc = be.fault(cl.domain, pg);
     if (rc != MS_OK) {
       cr.rc = rc;
       return;
@@ -74,27 +157,20 @@ void run_client(ms_server *srv, const ms_window_config &cfg, ClientRun &cr, uint
       std::vector<uint64_t> ev(window.begin(), window.begin() + (long)k);
       window.erase(window.begin(), window.begin() + (long)k);
       for (uint64_t e : ev) in_window.erase(e);
-      for (;;) {
-        rc = ms_server_submit_dom(srv, MS_ENCRYPT, cl.domain, ev.data(), (uint32_t)k, &ticket);
-        if (rc != MS_EBUSY) break;
-        std::this_thread::yield();
-      }
+      rc = be.evict(cl.domain, ev.data(), k);
       if (rc != MS_OK) {
         cr.rc = rc;
         return;
       }
       cr.st.evictions += k;
       cr.st.evict_requests += 1;
-      cr.evict_tickets.push_back(ticket);
     }
   }
   // the client's evictions complete before it reports
-  for (uint64_t t : cr.evict_tickets) {
-    const int rc = ms_server_wait(srv, t, timeout_ms);
-    if (rc != MS_OK) {
-      cr.rc = rc;
-      return;
-    }
+  const int rc = be.drain();
+  if (rc != MS_OK) {
+    cr.rc = rc;
+    return;
   }
   cr.st.elapsed_s = std::chrono::duration<double>(clk::now() - t0).count();
   cr.final_window.assign(window.begin(), window.end());
@@ -109,25 +185,33 @@ double percentile(std::vector<double> v, double q) {
   return v[lo] + (v[hi] - v[lo]) * (pos - (double)lo);
 }
 
-}  // namespace
-
-extern "C" int ms_window_run(ms_server *srv, const ms_window_config *cfg, const ms_window_client *clients,
-                             size_t n_clients, ms_window_stats *stats_out, uint64_t *final_window_out,
-                             uint32_t timeout_ms) {
-  if (!srv || !cfg || (n_clients && !clients)) return MS_EINVAL;
+int check_window_args(const ms_window_config *cfg, const ms_window_client *clients, size_t n_clients,
+                      uint64_t n_pages) {
+  if (!cfg || (n_clients && !clients)) return MS_EINVAL;
   if (cfg->window_pages == 0 || cfg->evict_batch == 0 || cfg->evict_batch > cfg->window_pages + 1) return MS_EINVAL;
   for (size_t c = 0; c < n_clients; ++c) {
     if (!clients[c].trace && clients[c].trace_len) return MS_EINVAL;
+    if (clients[c].first_page > n_pages || clients[c].n_pages > n_pages - clients[c].first_page) return MS_EINVAL;
     for (size_t d = 0; d < c; ++d) {  // clients own disjoint page ranges
       const ms_window_client &a = clients[c], &b = clients[d];
       if (a.first_page < b.first_page + b.n_pages && b.first_page < a.first_page + a.n_pages) return MS_EINVAL;
     }
   }
+  return MS_OK;
+}
+
+// One thread per client, each with its own backend; then the per-client report.
+template <typename MakeBackend>
+int run_clients(const ms_window_config &cfg, const ms_window_client *clients, size_t n_clients,
+                ms_window_stats *stats_out, uint64_t *final_window_out, MakeBackend make) {
   std::vector<ClientRun> runs(n_clients);
   std::vector<std::thread> th;
   for (size_t c = 0; c < n_clients; ++c) {
     runs[c].cl = &clients[c];
-    th.emplace_back([&, c] { run_client(srv, *cfg, runs[c], timeout_ms); });
+    th.emplace_back([&, c] {
+      auto be = make(clients[c]);
+      run_client(be, cfg, runs[c]);
+    });
   }
   for (auto &t : th) t.join();
   int rc = MS_OK;
@@ -141,10 +225,42 @@ extern "C" int ms_window_run(ms_server *srv, const ms_window_config *cfg, const 
     if (stats_out) stats_out[c] = r.st;
     if (final_window_out) {
       // client c's final window goes to final_window_out[c * (window_pages + 1) ...], oldest first
-      uint64_t *dst = final_window_out + c * ((size_t)cfg->window_pages + 1);
-      for (size_t i = 0; i < (size_t)cfg->window_pages + 1; ++i)
+      uint64_t *dst = final_window_out + c * ((size_t)cfg.window_pages + 1);
+      for (size_t i = 0; i < (size_t)cfg.window_pages + 1; ++i)
         dst[i] = i < r.final_window.size() ? r.final_window[i] : ~0ull;
     }
   }
   return rc;
+}
+
+}  // namespace
+
+extern "C" int ms_window_run(ms_server *srv, const ms_window_config *cfg, const ms_window_client *clients,
+                             size_t n_clients, ms_window_stats *stats_out, uint64_t *final_window_out,
+                             uint32_t timeout_ms) {
+  if (!srv) return MS_EINVAL;
+  const int rc = check_window_args(cfg, clients, n_clients, ~0ull);
+  if (rc != MS_OK) return rc;
+  return run_clients(*cfg, clients, n_clients, stats_out, final_window_out, [&](const ms_window_client &) {
+    return ServerBackend{srv, timeout_ms, {}};
+  });
+}
+
+extern "C" int ms_window_run_resident(ms_resident *res, void *host_base, uint64_t n_pages,
+                                      const ms_window_config *cfg, const ms_window_client *clients,
+                                      size_t n_clients, ms_window_stats *stats_out, uint64_t *final_window_out,
+                                      uint32_t timeout_ms) {
+  if (!res || !host_base || n_pages == 0) return MS_EINVAL;
+  const int rc = check_window_args(cfg, clients, n_clients, n_pages);
+  if (rc != MS_OK) return rc;
+  void *dbase = nullptr;
+  if (cudaHostGetDevicePointer(&dbase, host_base, 0) != cudaSuccess || !dbase) {
+    cudaGetLastError();
+    return MS_EINVAL;  // the working set must be pinned, mapped memory
+  }
+  return run_clients(*cfg, clients, n_clients, stats_out, final_window_out, [&](const ms_window_client &cl) {
+    ResidentBackend be{res, (uint64_t)dbase, cl.first_page, timeout_ms, {}, {}};
+    be.last_ticket.assign(cl.n_pages, ~0ull);
+    return be;
+  });
 }

@@ -193,6 +193,8 @@ def _load():
         "ms_resident_replay": (I, [P, P, U64, S, P, P, P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.c_uint32]),
         "ms_window_run": (I, [P, ctypes.POINTER(ms_window_config), ctypes.POINTER(ms_window_client), S,
                               ctypes.POINTER(ms_window_stats), P, ctypes.c_uint32]),
+        "ms_window_run_resident": (I, [P, P, U64, ctypes.POINTER(ms_window_config), ctypes.POINTER(ms_window_client),
+                                       S, ctypes.POINTER(ms_window_stats), P, ctypes.c_uint32]),
         "ms_crypt_pages_dom_dev": (I, [P, P, S]),
         "ms_server_get_stats": (I, [P, ctypes.POINTER(ms_server_stats)]),
         "ms_server_destroy": (I, [P]),
@@ -529,23 +531,8 @@ class Server:
     def run_window_clients(self, window_pages: int, evict_batch: int, clients, timeout_ms: int = 60000):
         """Sliding-window clients: `clients` is a list of (domain, first_page, n_pages, trace).
         Returns (per-client stats dicts, per-client final windows as lists of page indices)."""
-        cfg = ms_window_config(window_pages, evict_batch)
-        arr = (ms_window_client * len(clients))()
-        keep = []
-        for i, (dom, first, n, trace) in enumerate(clients):
-            tr = np.ascontiguousarray(trace, dtype=np.uint64)
-            keep.append(tr)
-            arr[i] = ms_window_client(dom, 0, first, n, tr.ctypes.data, tr.size)
-        st = (ms_window_stats * len(clients))()
-        fw = np.empty(len(clients) * (window_pages + 1), dtype=np.uint64)
-        _check(_lib.ms_window_run(self.handle, ctypes.byref(cfg), arr, len(clients), st, fw.ctypes.data, timeout_ms),
-               "ms_window_run")
-        stats = [{f: getattr(st[i], f) for f, _ in ms_window_stats._fields_} for i in range(len(clients))]
-        wins = []
-        for i in range(len(clients)):
-            w = fw[i * (window_pages + 1):(i + 1) * (window_pages + 1)]
-            wins.append([int(x) for x in w if x != np.uint64(0xFFFFFFFFFFFFFFFF)])
-        return stats, wins
+        return _run_window(lambda cfg, arr, n, st, fw: _lib.ms_window_run(self.handle, cfg, arr, n, st, fw, timeout_ms),
+                           "ms_window_run", window_pages, evict_batch, clients)
 
     def stats(self) -> dict:
         st = ms_server_stats()
@@ -564,6 +551,25 @@ class Server:
 
     def __exit__(self, *exc):
         self.destroy()
+
+
+def _run_window(call, name: str, window_pages: int, evict_batch: int, clients):
+    cfg = ms_window_config(window_pages, evict_batch)
+    arr = (ms_window_client * len(clients))()
+    keep = []
+    for i, (dom, first, n, trace) in enumerate(clients):
+        tr = np.ascontiguousarray(trace, dtype=np.uint64)
+        keep.append(tr)
+        arr[i] = ms_window_client(dom, 0, first, n, tr.ctypes.data, tr.size)
+    st = (ms_window_stats * len(clients))()
+    fw = np.empty(len(clients) * (window_pages + 1), dtype=np.uint64)
+    _check(call(ctypes.byref(cfg), arr, len(clients), st, fw.ctypes.data), name)
+    stats = [{f: getattr(st[i], f) for f, _ in ms_window_stats._fields_} for i in range(len(clients))]
+    wins = []
+    for i in range(len(clients)):
+        w = fw[i * (window_pages + 1):(i + 1) * (window_pages + 1)]
+        wins.append([int(x) for x in w if x != np.uint64(0xFFFFFFFFFFFFFFFF)])
+    return stats, wins
 
 
 class Resident:
@@ -619,6 +625,15 @@ class Resident:
                                        page_index.ctypes.data, lat.ctypes.data, ctypes.byref(mk), timeout_ms),
                "ms_resident_replay")
         return lat, mk.value
+
+    def run_window_clients(self, host_base, n_pages: int, window_pages: int, evict_batch: int, clients,
+                           timeout_ms: int = 60000):
+        """The sliding-window clients of Server.run_window_clients, served by these
+        workers in place on a pinned, mapped working set of n_pages pages."""
+        base = _ptr(host_base)
+        return _run_window(lambda cfg, arr, n, st, fw: _lib.ms_window_run_resident(
+            self.handle, base, n_pages, cfg, arr, n, st, fw, timeout_ms),
+            "ms_window_run_resident", window_pages, evict_batch, clients)
 
     def destroy(self) -> int:
         if self.handle:

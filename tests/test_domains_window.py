@@ -109,6 +109,38 @@ def test_sliding_window_clients(ms, key1, window, batch):
         assert st["fault_p50_us"] > 0 and st["fault_p99_us"] >= st["fault_p50_us"]
 
 
+@pytest.mark.parametrize("window,batch", [(4, 1), (8, 4), (16, 9)])
+def test_sliding_window_clients_on_resident_workers(ms, key1, window, batch):
+    """The same clients served by resident workers in place on the pinned working
+    set: the same final state (final-window pages in clear, the rest encrypted
+    under each client's PID)."""
+    per, n_clients = 128, 3
+    n = per * n_clients + 5                     # pages past the clients stay untouched
+    plain = synth.page_bytes_fast(196, 0, n)
+    h = torch.from_numpy(plain.copy()).pin_memory()
+    doms = [11, 22, 33]
+    clients = [(doms[c], c * per, per, synth.window_trace(197 + c, per, 1500)) for c in range(n_clients)]
+    with ms.Context(key1) as ctx:
+        with ms.Server(ctx, h, n) as srv:
+            for c in range(n_clients):
+                srv.wait(srv.submit(ms.MS_ENCRYPT, np.arange(c * per, (c + 1) * per), domain=doms[c]))
+        with ms.Resident(ctx, workers=4) as res:
+            stats, wins = res.run_window_clients(h, n, window, batch, clients)
+    ws = h.numpy()
+    for c in range(n_clients):
+        st, win = stats[c], wins[c]
+        assert st["accesses"] == 1500 and st["hits"] + st["faults"] == 1500
+        assert st["faults"] - st["evictions"] == len(win) <= window
+        enc = np.array(sorted(set(range(c * per, (c + 1) * per)) - set(win)), dtype=np.uint64)
+        want = plain[c * per * PAGE:(c + 1) * per * PAGE].copy()
+        oracle.crypt_pages(key1, want, enc - np.uint64(c * per), enc, domain=doms[c])
+        assert np.array_equal(ws[c * per * PAGE:(c + 1) * per * PAGE], want), f"client {c}"
+    assert np.array_equal(ws[n_clients * per * PAGE:], plain[n_clients * per * PAGE:])
+    with ms.Context(key1) as ctx, ms.Resident(ctx) as res:
+        with pytest.raises(ms.MemShieldError):                 # a client range past the working set
+            res.run_window_clients(h, n, 4, 1, [(1, n - 4, 8, np.zeros(2, dtype=np.uint64))])
+
+
 def test_window_rejects_bad_configs(ms, key1):
     n = 64
     h = torch.zeros(n * PAGE, dtype=torch.uint8).pin_memory()
