@@ -34,8 +34,9 @@
 namespace {
 
 enum : uint32_t { kRunning = 1, kExiting = 2, kExited = 3 };
-constexpr int kWorkerThreads = 256;          // 4 pages in parallel at 64 threads per page
+constexpr int kWorkerThreads = 512;          // 8 pages in parallel at 64 threads per page
 constexpr int kPagesPerPass = kWorkerThreads / 64;
+static_assert(kPagesPerPass <= 32, "one lane of warp 0 per ring slot of a pass");
 
 struct alignas(32) RingEntry {
   uint64_t addr;
@@ -86,54 +87,82 @@ __device__ __forceinline__ void st_release_sys32(uint32_t *p, uint32_t v) {
   asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// One pass: warp 0 looks at the next kPagesPerPass ring slots at once (lane k
+// reads slot i + k: its sequence word with a system-scope acquire, then the
+// entry), and the pass takes the leading run of published slots; every page
+// of the pass is processed by 64 threads in parallel; then lanes 0..n-1
+// publish the done words together.  Host-link round trips per pass: one for
+// the sequence words, one for the entries, however many pages are taken.
 __global__ void __launch_bounds__(kWorkerThreads) k_resident(const ResidentArgs a) {
   __shared__ RingEntry s_e[kPagesPerPass];
   __shared__ int s_n;
   const uint32_t tid = threadIdx.x;
+  const uint32_t lane = tid % 32;
   uint64_t i = a.sh->next;  // written by the previous launch / the host before this launch
   const uint64_t t_start = gtime();
   uint64_t t_last = t_start;
+  bool busy = false;  // warp 0: the last pass took a full kPagesPerPass
   ms::BlockSeed s;
   ms::load_key(a.key, s.k);
   for (;;) {
-    if (tid == 0) {
+    if (tid < 32) {
       int n = 0;
-      const uint64_t now = gtime();
-      if (ld_volatile_u32(&a.sh->stop) != 0 || now - t_start > a.max_ns) {
+      // lane 0's clock and stop word decide for the whole warp (the warp-wide
+      // vote and shuffles below need every lane on the same path)
+      uint64_t now = gtime();
+      now = __shfl_sync(0xffffffffu, now, 0);
+      int leave = lane == 0 && (ld_volatile_u32(&a.sh->stop) != 0 || now - t_start > a.max_ns);
+      leave = __shfl_sync(0xffffffffu, leave, 0);
+      if (leave) {
         // stop, or this launch has run long enough: leave even with work
         // queued; the host launches the worker again when it waits or submits
-        a.sh->next = i;
-        if (now - t_start > a.max_ns) a.sh->timeouts += 1;
-        __threadfence_system();
-        st_release_sys32(&a.sh->state, kExited);
+        if (lane == 0) {
+          a.sh->next = i;
+          if (now - t_start > a.max_ns) a.sh->timeouts += 1;
+          __threadfence_system();
+          st_release_sys32(&a.sh->state, kExited);
+        }
         n = -1;
       } else {
-        for (int k = 0; k < kPagesPerPass; ++k) {
-          const RingEntry *e = a.ring + ((i + k) & a.ring_mask);
-          if (ld_acquire_sys(&e->seq) != i + k + 1) break;
-          s_e[k] = *e;
-          ++n;
-        }
+        const RingEntry *e = a.ring + ((i + lane) & a.ring_mask);
+        // While the ring was idle only slot i is watched (one 8-byte read per
+        // poll over the host link); after a full pass, all slots are read at once.
+        const uint32_t watch = busy ? (uint32_t)kPagesPerPass : 1u;
+        bool ready = lane < watch && ld_acquire_sys(&e->seq) == i + lane + 1;
+        if (!busy && __shfl_sync(0xffffffffu, (int)ready, 0))
+          ready = lane == 0 || (lane < (uint32_t)kPagesPerPass && ld_acquire_sys(&e->seq) == i + lane + 1);
+        const uint32_t mask = __ballot_sync(0xffffffffu, ready);
+        n = __ffs(~mask) - 1;  // the leading run of published slots, in ring order
+        busy = n == kPagesPerPass;
+        if ((int)lane < n) s_e[lane] = *e;
         if (n > 0) {
           t_last = now;
         } else if (now - t_last > a.idle_ns) {
-          st_release_sys32(&a.sh->state, kExiting);
-          __threadfence_system();
-          const RingEntry *e = a.ring + (i & a.ring_mask);
-          if (ld_acquire_sys(&e->seq) == i + 1) {
-            st_release_sys32(&a.sh->state, kRunning);  // a request raced the exit: stay
+          int stay = 0;
+          if (lane == 0) {
+            st_release_sys32(&a.sh->state, kExiting);
+            __threadfence_system();
+            const RingEntry *e0 = a.ring + (i & a.ring_mask);
+            if (ld_acquire_sys(&e0->seq) == i + 1) {
+              st_release_sys32(&a.sh->state, kRunning);  // a request raced the exit: stay
+              stay = 1;
+            } else {
+              a.sh->next = i;
+              __threadfence_system();
+              st_release_sys32(&a.sh->state, kExited);
+            }
+          }
+          stay = __shfl_sync(0xffffffffu, stay, 0);
+          if (stay) {
             t_last = now;
           } else {
-            a.sh->next = i;
-            __threadfence_system();
-            st_release_sys32(&a.sh->state, kExited);
             n = -1;
           }
-        } else {
+        } else if (lane == 0) {
           __nanosleep(256);
         }
       }
-      s_n = n;
+      if (lane == 0) s_n = n;
     }
     __syncthreads();
     const int n = s_n;
@@ -151,8 +180,7 @@ __global__ void __launch_bounds__(kWorkerThreads) k_resident(const ResidentArgs 
       }
       __threadfence_system();  // this thread's page writes are visible before the done word
       __syncthreads();
-      if (tid == 0)
-        for (int k = 0; k < n; ++k) st_release_sys(a.done + ((i + k) & a.ring_mask), i + k + 1);
+      if (tid < (uint32_t)n) st_release_sys(a.done + ((i + tid) & a.ring_mask), i + tid + 1);
       i += n;
     }
     __syncthreads();
