@@ -355,7 +355,7 @@ def run_ours(args):
         "e2e": e2e,
     }
     if not args.no_serving and world == 1:
-        rows, _ = serve_rows(args, [1.41e5, 2e6], ["continuous", "one_per_launch"], 2.0)
+        rows, _ = serve_rows(args, [1.41e5, 2e6], ["continuous", "one_per_launch", "resident"], 2.0)
         line["serving"] = {
             "workload": SERVE_WORKLOAD.format(n=args.serve_pages, gib=args.serve_pages * PAGE / 2**30, sec=2.0),
             "rows": [{k: r[k] for k in ("offered_pages_per_s", "mode", "sustained_pages_per_s", "p50_us", "p99_us",
