@@ -181,10 +181,12 @@ int ms_shutdown(ms_ctx *ctx);
  *                      blocks; needs blocks_per_thread >= 2, dr_unroll =
  *                      rounds / 2, rot_policy 0 or 1
  * ms_set_shape returns MS_EINVAL (and changes nothing) for a shape that is
- * not compiled for the context's round count.  Until a shape is set (here,
- * in ms_config or by ms_tune_load), a one-launch call whose pages would not
- * fill the GPU with the default shape runs with 1 block per thread, which
- * finishes small launches sooner; a set shape is always used as it is.
+ * not compiled for the context's round count.  Until a shape is set (here or
+ * in ms_config), a one-launch call whose pages would not fill the GPU with
+ * the default (or tuned: ms_autotune, ms_tune_load) shape runs with 1 block
+ * per thread, which finishes small launches sooner, and host lists of up to
+ * 1024 entries travel in the kernel parameters; a set shape is always used
+ * as it is.
  */
 typedef struct ms_shape {
   uint32_t blocks_per_thread;

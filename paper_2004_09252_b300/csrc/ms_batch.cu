@@ -241,7 +241,7 @@ int ms_batch_create(ms_ctx *c, const ms_batch_config *cfg_in, ms_batch **out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q.copied, cudaEventDisableTiming);
     if (e != cudaSuccess) {
       free_batch(b);
-      return e == cudaErrorMemoryAllocation ? MS_ENOMEM : cuda_fail(c, e);
+      return alloc_fail(c, e);
     }
     std::memset(q.h, 0, kHeader);
   }

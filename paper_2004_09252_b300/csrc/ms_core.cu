@@ -19,7 +19,14 @@ namespace ms {
 
 int cuda_fail(ms_ctx *c, cudaError_t e) {
   if (c) c->last_cuda.store((int)e);
+  cudaGetLastError();  // a non-sticky error must not be reported again by the next launch check
   return MS_ECUDA;
+}
+
+int alloc_fail(ms_ctx *c, cudaError_t e) {
+  if (e != cudaErrorMemoryAllocation) return cuda_fail(c, e);
+  cudaGetLastError();  // out of memory is not sticky: clear it for the next launch check
+  return MS_ENOMEM;
 }
 
 // Moves the device status word to the mapped host word and clears it: one
@@ -231,6 +238,7 @@ int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg_in) {
     e = (call);                      \
     if (e != cudaSuccess) {          \
       int rc = (e == cudaErrorMemoryAllocation) ? MS_ENOMEM : MS_ECUDA; \
+      cudaGetLastError();            \
       release(c);                    \
       return rc;                     \
     }                                \
@@ -456,7 +464,7 @@ int ms_crypt_host(ms_ctx *c, int op, void *host_base, uint64_t first_page_id, si
     }
     if (!c->hs_buf[i]) {
       e = cudaMalloc(&c->hs_buf[i], c->hs_cap);
-      if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MS_ENOMEM : cuda_fail(c, e);
+      if (e != cudaSuccess) return alloc_fail(c, e);
     }
   }
   // order after earlier work on the context stream

@@ -62,7 +62,7 @@ struct ms_ctx {
                                      // those can set a status bit (every other entry is checked
                                      // on the host or built by the library)
   ms::Tune tune;
-  bool shape_explicit = false;  // set by the caller (config, ms_set_shape, a loaded table): never adapted
+  bool shape_explicit = false;  // set by the caller (config, ms_set_shape): never adapted
   ms::QTune qtune;
   std::atomic<unsigned> tune_gen{0};  // bumped whenever tune/qtune change
   ms::ListSlot slots[ms::kListSlots];
@@ -96,7 +96,11 @@ class DeviceGuard {
   int prev_ = 0, dev_ = 0;
 };
 
+// Records a CUDA error on the context (ms_last_cuda_error), clears the
+// runtime's last-error state and returns MS_ECUDA.
 int cuda_fail(ms_ctx *c, cudaError_t e);
+// Allocation failure: MS_ENOMEM for out of memory (state cleared), else cuda_fail.
+int alloc_fail(ms_ctx *c, cudaError_t e);
 
 // Host-side fault injection (tests): returns the injected error when the
 // armed countdown reaches zero at a site in the armed mask, else cudaSuccess.

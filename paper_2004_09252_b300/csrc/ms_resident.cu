@@ -317,7 +317,7 @@ int ms_resident_create(ms_ctx *c, const ms_resident_config *cfg_in, ms_resident 
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
       free_resident(r);
-      return e == cudaErrorMemoryAllocation ? MS_ENOMEM : cuda_fail(c, e);
+      return alloc_fail(c, e);
     }
     std::memset(w->h_ring, 0, sizeof(RingEntry) * cfg.ring_entries);
     std::memset(w->h_done, 0, sizeof(uint64_t) * cfg.ring_entries);

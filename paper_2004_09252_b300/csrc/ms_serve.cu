@@ -497,7 +497,7 @@ int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_serv
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_work[1], cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     free_server(s);
-    return e == cudaErrorMemoryAllocation ? MS_ENOMEM : cuda_fail(c, e);
+    return alloc_fail(c, e);
   }
   try {
     s->reqs = std::vector<Req>(cfg.max_pending);

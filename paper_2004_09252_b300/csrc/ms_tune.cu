@@ -80,7 +80,7 @@ int ms_autotune(ms_ctx *c, size_t sample_pages, ms_tune_result *out) {
   if (e == cudaSuccess) e = cudaMalloc(&x.hdr, 2 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaEventCreate(&x.a);
   if (e == cudaSuccess) e = cudaEventCreate(&x.b);
-  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? MS_ENOMEM : cuda_fail(c, e);
+  if (e != cudaSuccess) return alloc_fail(c, e);
   cudaStream_t s = c->stream;
   e = cudaMemsetAsync(x.pages, 0, sample_pages * MS_PAGE_BYTES, s);
   // scattered list: a fixed pseudo-random permutation of the sample's slots
@@ -213,8 +213,7 @@ int ms_tune_load(ms_ctx *c, const char *path) {
   if (tag != device_tag(c->device, c->sm_count) || rounds != (int)c->cfg.rounds) return MS_EINVAL;
   if (!shape_available(rounds, t) || q.grab < 1 || q.grab > 4096 || q.ctas_per_sm < 0) return MS_EINVAL;
   std::lock_guard<std::mutex> lk(c->mu);
-  c->tune = t;
-  c->shape_explicit = true;
+  c->tune = t;  // like a tuning run's result: small launches may still adapt it
   c->qtune = q;
   c->tune_gen.fetch_add(1);
   return MS_OK;
