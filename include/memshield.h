@@ -142,6 +142,8 @@ int ms_crypt_pages_dom_dev(ms_ctx *ctx, const ms_page_dom *d_pages, size_t n);
 /*
  * Contiguous form: n_pages pages back to back at the device address d_base
  * (16-byte aligned); page k has id first_page_id + k.  No entry list is read.
+ * MS_EINVAL when the ids would wrap past 2^64 - 1 (a wrapped id would reuse
+ * another page's keystream).
  */
 int ms_crypt_range(ms_ctx *ctx, int op, void *d_base, uint64_t first_page_id, size_t n_pages);
 
@@ -228,7 +230,8 @@ int ms_debug_inject_fault(int site_mask, int countdown, int cuda_error);
  * goes host->device, through the cipher and back on stream i % n_streams
  * (n_streams 1..4, 0 = 2) with its own device buffer, so copies in both
  * directions overlap the kernels.  Returns when the results are back in
- * host memory (bounded by timeout_ms per chunk).
+ * host memory (bounded by timeout_ms per chunk).  MS_EINVAL when the ids
+ * would wrap past 2^64 - 1.
  */
 int ms_crypt_host(ms_ctx *ctx, int op, void *host_base, uint64_t first_page_id, size_t n_pages,
                   size_t chunk_bytes, int n_streams);

@@ -237,6 +237,40 @@ def test_short_host_lists_back_to_back(ms, key1):
     assert np.array_equal(d.cpu().numpy(), oracle_expected(key1, plain, all_, all_))
 
 
+def test_extreme_ids_and_domains(ms, key1):
+    """Ids at the edges of the 64-bit range (nonce words 13 and 14 all ones, or
+    one of them zero) and the largest domain word, through the host list, the
+    device list and the range form; a range whose ids would wrap is refused."""
+    ids = np.array([0, 1, 2**32 - 1, 2**32, 2**63, 2**64 - 2, 2**64 - 1, 0xFFFFFFFF00000000], dtype=np.uint64)
+    n = ids.size
+    plain = synth.page_bytes(170, 0, n)
+    slots = np.arange(n, dtype=np.uint64)
+    for dom in (0, 0xFFFFFFFF):
+        want = oracle_expected(key1, plain, slots, ids, domain=dom)
+        with make_ctx(ms, key1, domain=dom) as ctx:
+            d = dev(plain)
+            ctx.encrypt_pages(ms.pages_array(d.data_ptr() + PAGE * slots, ids))
+            ctx.sync_checked()
+            assert np.array_equal(d.cpu().numpy(), want)
+            d = dev(plain)
+            lst = torch.from_numpy(ms.pages_array(d.data_ptr() + PAGE * slots, ids).view(np.uint8)).cuda()
+            ctx.encrypt_pages_dev(lst, n)
+            ctx.sync_checked()
+            assert np.array_equal(d.cpu().numpy(), want)
+            d = dev(plain[:2 * PAGE])                      # the last two ids of the space
+            ctx.crypt_range(ms.MS_ENCRYPT, d, 2**64 - 2, 2)
+            ctx.sync_checked()
+            assert np.array_equal(d.cpu().numpy(), oracle_expected(key1, plain[:2 * PAGE], np.arange(2), ids[5:7],
+                                                                   domain=dom))
+            with pytest.raises(ms.MemShieldError) as e:   # 2^64 - 1, then 0: refused, nothing runs
+                ctx.crypt_range(ms.MS_ENCRYPT, d, 2**64 - 1, 2)
+            assert e.value.code == ms.MS_EINVAL
+            h = torch.from_numpy(plain[:2 * PAGE].copy()).pin_memory()
+            with pytest.raises(ms.MemShieldError):
+                ctx.crypt_host(ms.MS_ENCRYPT, h, 2**64 - 1, 2)
+            assert np.array_equal(h.numpy(), plain[:2 * PAGE])
+
+
 @pytest.mark.slow
 def test_bulk_1gib_sampled(ms, key1):
     """The 1 GiB bulk configuration in the launch shape the benchmark times:
