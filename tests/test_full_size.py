@@ -37,20 +37,27 @@ def test_host_config_4gib(ms, key1):
         assert np.array_equal(hv[p], synth.page_bytes(4, int(p), 1))
 
 
-def test_serving_config_16gib(ms, key1):
-    """One second of the serving mix at 141k pages/s over the 16 GiB working
-    set (seed 5), continuous batching: every touched page ends as the closed
-    form says (odd number of applications = encrypted)."""
+@pytest.mark.parametrize("form,rate,n_req", [("continuous", 1.41e5, 17625), ("resident", 2e6, 250000)])
+def test_serving_config_16gib(ms, key1, form, rate, n_req):
+    """The serving mix over the 16 GiB working set (seed 5): one second at
+    141k pages/s through continuous batching, and one second at 2M pages/s
+    through resident workers (8 workers, in place). Every touched page ends as
+    the closed form says (odd number of applications = encrypted)."""
     n = 4194304
     ws = torch.empty(n * PAGE, dtype=torch.uint8).pin_memory()
     synth.fill_pages(ws.data_ptr(), 5, 0, n)
-    arrival, ops, offsets, pages = synth.serving_workload(5, 17625, 1.41e5, n)
-    with ms.Context(key1) as ctx, ms.Server(ctx, ws, n) as srv:
-        lat, makespan = srv.replay(arrival, ops, offsets, pages)
+    arrival, ops, offsets, pages = synth.serving_workload(5, n_req, rate, n)
+    with ms.Context(key1) as ctx:
+        if form == "resident":
+            with ms.Resident(ctx, workers=8) as res:
+                lat, makespan = res.replay(ws, n, arrival, offsets, pages)
+        else:
+            with ms.Server(ctx, ws, n) as srv:
+                lat, makespan = srv.replay(arrival, ops, offsets, pages)
     assert (lat >= 0).all()
     counts = np.bincount(pages.astype(np.int64), minlength=n)
     touched = np.nonzero(counts)[0]
-    pick = touched[(synth.splitmix64(132, 0, 64) % np.uint64(len(touched))).astype(np.int64)]
+    pick = touched[(synth.splitmix64(132, 0, 256) % np.uint64(len(touched))).astype(np.int64)]
     wv = ws.numpy().reshape(n, PAGE)
     for p in pick:
         pg = synth.page_bytes(5, int(p), 1)
