@@ -797,7 +797,8 @@ def run_reference(args):
     per_page = (time.perf_counter() - t0) / 32
     budget = min(150.0, max(20.0, 1.5 * (args.steps + args.warmup)))
     step_s = budget / (args.steps + args.warmup)
-    npg = int(max(threads * 4, min(BULK_PAGES, step_s / per_page * threads / 2)))
+    # a step is two passes (encrypt + decrypt); assume half-linear thread scaling
+    npg = int(max(threads * 4, min(BULK_PAGES, step_s / (2 * per_page) * threads / 2)))
     buf = synth.page_bytes_fast(2, 0, npg)
     ids = np.arange(npg, dtype=np.uint64)
     for _ in range(args.warmup):
