@@ -504,16 +504,24 @@ def run_batching(args):
     results = []
     applied = 0
     for breq in args.batch_requests:
+        # a fixed number of requests per submit, or "rA-B": A requests first,
+        # doubling on every submit up to B (the first kernel starts sooner, and
+        # each fill still overlaps the previous submit's kernel)
+        if isinstance(breq, str):
+            size, cap = (int(x) for x in breq[1:].split("-"))
+        else:
+            size = cap = breq
         with ctx.batch(capacity=max(1 << 16, int(total))) as bt:
             torch.cuda.synchronize()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             t0 = time.perf_counter()
             ev0.record(stream)
-            first = 0
+            first, step = 0, size
             while first < n_req:
-                rc, added = bt.add_requests(ops, offsets, table_a, first, min(breq, n_req - first))
+                rc, added = bt.add_requests(ops, offsets, table_a, first, min(step, n_req - first))
                 first += added
                 bt.submit()
+                step = min(cap, 2 * step)
             ev1.record(stream)
             if ctx.sync():
                 raise RuntimeError("sync failed")
@@ -863,8 +871,9 @@ def main():
                     help="continuous serving: waves up to this many pages run in place (default: library's)")
     ap.add_argument("--idle-spin-us", type=int, default=None, help="serving idle poll window (default: library's)")
     ap.add_argument("--serve-modes", type=lambda v: v.split(","), default=["continuous", "one_per_launch"])
-    ap.add_argument("--batch-requests", type=lambda v: [int(x) for x in v.split(",")],
-                    default=[1, 16, 256, 2000, 20000])
+    ap.add_argument("--batch-requests", type=lambda v: [x if x.startswith("r") else int(x) for x in v.split(",")],
+                    default=[1, 16, 256, 2000, 20000, "r60-4000"],
+                    help="requests per submit; rA-B = A first, doubling per submit up to B")
     ap.add_argument("--chunks-mib", type=lambda v: [int(x) for x in v.split(",")], default=[2, 4, 8, 16, 32, 64])
     args = ap.parse_args()
     if args.warmup < 3:

@@ -274,7 +274,10 @@ typedef struct ms_batch_stats {
 } ms_batch_stats;
 
 void ms_batch_config_default(ms_batch_config *cfg);
-/* Allocates two pinned + two device queue buffers of 256 + 16 * capacity bytes. */
+/* Allocates two pinned + two device queue buffers of 256 + 16 * capacity bytes
+ * (32 * capacity with per_page_domain) and, with use_graph, captures the CUDA
+ * graph of each buffer, so that no submit pays for a capture (a later change
+ * of the context's tuning recaptures at the next submit). */
 int ms_batch_create(ms_ctx *ctx, const ms_batch_config *cfg, ms_batch **out);
 /* Append one request (op is bookkeeping: encryption = decryption).  Entries are
  * checked on the host (MS_EINVAL).  MS_EBUSY: the batch is full, submit first;

@@ -245,6 +245,17 @@ int ms_batch_create(ms_ctx *c, const ms_batch_config *cfg_in, ms_batch **out) {
     }
     std::memset(q.h, 0, kHeader);
   }
+  if (cfg.use_graph) {
+    // capture both buffers' graphs now, so that no submit pays for it
+    std::lock_guard<std::mutex> lk(c->mu);
+    for (QBuf &q : b->buf) {
+      const cudaError_t e = capture(b, q);
+      if (e != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail(c, e);
+      }
+    }
+  }
   c->children.fetch_add(1);
   *out = b;
   return MS_OK;
