@@ -81,3 +81,19 @@ def test_struct_layout_matches_c():
                     cfg.timeout_ms.offset, cfg.use_stream.offset, ctypes.sizeof(m.ms_batch_config),
                     ctypes.sizeof(m.ms_batch_stats), ctypes.sizeof(m.ms_tune_result),
                     m.ms_tune_result.queue_gbs.offset, m.ms_tune_result.tried.offset]
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No CPU fallback: importing the binding where the library is not built
+    (and may not be built) raises instead of running anything."""
+    import shutil
+    import sys
+    pkg = os.path.join(ROOT, "paper_2004_09252_b300")
+    dst = tmp_path / "paper_2004_09252_b300"
+    dst.mkdir()
+    for f in ("__init__.py", "build.py", "memshield.py"):
+        shutil.copy(os.path.join(pkg, f), dst / f)
+    env = dict(os.environ, MEMSHIELD_NO_BUILD="1", PYTHONPATH=str(tmp_path))
+    r = subprocess.run([sys.executable, "-c", "from paper_2004_09252_b300 import memshield"], cwd=tmp_path, env=env,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0 and "libmemshield.so not built" in r.stderr
