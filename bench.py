@@ -321,6 +321,7 @@ def run_ours(args):
         del hbuf
 
     ctx.shutdown()
+    pipes = ms.probe_int_pipes(dev)  # the op-class rates the ALU-pipe peak below assumes
     line = {
         "metric": "page encrypt GB/s (ChaCha20, 4 KiB pages, device-resident)",
         "value": round(value, 3),
@@ -350,7 +351,8 @@ def run_ours(args):
                      "alu_pipe": {"peak": round(alu_pipe_peak, 3), "frac": round(achieved / alu_pipe_peak, 4),
                                   "note": f"{props.multi_processor_count} SMs x {ALU_PIPE_LANES_PER_SM} lanes x "
                                           f"{sm_max:.0f} MHz on the xor/rotate pipe, x {OPS_PER_BLOCK}/"
-                                          f"{ALU_PIPE_OPS_PER_BLOCK} algorithmic ops per pipe op"},
+                                          f"{ALU_PIPE_OPS_PER_BLOCK} algorithmic ops per pipe op",
+                                  "probe_lanes_per_sm_clk": {r["class"]: r["lanes_per_sm_clk"] for r in pipes}},
                      "hbm": {"achieved_gbs": round(alg_bytes / avg_launch_s / 1e9, 1),
                              "peak_gbs": peaks.get("hbm_gbs"),
                              "frac": round(alg_bytes / avg_launch_s / 1e9 / float(peaks.get("hbm_gbs", 6400.0)), 4),
@@ -786,6 +788,24 @@ def run_window(args):
         "rows": rows}), flush=True)
 
 
+# ------------------------------------------------------------ pipe rates
+def run_pipes(args):
+    """Sustained rates of the cipher's 32-bit op classes (ms_probe_int_pipes),
+    alone and in 1:1 mixes: the measurement behind the ALU-pipe roofline."""
+    import torch
+
+    from paper_2004_09252_b300 import memshield as ms
+    dev = torch.cuda.current_device()
+    rows = ms.probe_int_pipes(dev)
+    props = torch.cuda.get_device_properties(dev)
+    print(json.dumps({
+        "metric": "int32 lane operations per SM per clock, by op class", "unit": "lanes/SM/clk",
+        "value": next(r["lanes_per_sm_clk"] for r in rows if r["class"] == "xor"), "higher_is_better": True,
+        "config": {"workload": "4 CTAs x 256 threads per SM, 8 independent chains x 16384 ops per thread",
+                   "sms": props.multi_processor_count},
+        "rows": rows}), flush=True)
+
+
 # -------------------------------------------------------------- reference
 def run_reference(args):
     rank, world, _ = env_rank()
@@ -848,7 +868,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-chunk-mib", type=int, default=16)
     ap.add_argument("--e2e-streams", type=int, default=2)
-    ap.add_argument("--workload", choices=["bulk", "small", "batching", "host", "serving", "window"], default="bulk",
+    ap.add_argument("--workload", choices=["bulk", "small", "batching", "host", "serving", "window", "pipes"],
+                    default="bulk",
                     help="bulk (default, the contract line); batching / host / serving print their own line")
     ap.add_argument("--serve-pages", type=int, default=4194304, help="working-set pages (default 16 GiB)")
     ap.add_argument("--serve-rates", type=lambda v: [float(x) for x in v.split(",")], default=SERVE_RATES)
@@ -882,6 +903,8 @@ def main():
         run_reference(args)
     elif args.workload == "small":
         run_small(args)
+    elif args.workload == "pipes":
+        run_pipes(args)
     elif args.workload == "batching":
         run_batching(args)
     elif args.workload == "host":

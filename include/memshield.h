@@ -575,6 +575,42 @@ int ms_window_run_resident(ms_resident *res, void *host_base, uint64_t n_pages, 
 #define MS_NOALLOC_MAX_PAGES 16384u
 int ms_crypt_pages_noalloc(ms_ctx *ctx, int op, const ms_page *pages, size_t n);
 
+/*
+ * ---- Measurement: integer pipe rates (the paper has no counterpart) ----
+ *
+ * Sustained rates of the 32-bit op classes the cipher is built from, alone
+ * and in 1:1 mixes, on `device`: a grid of 4 CTAs of 256 threads per SM,
+ * each thread 8 independent chains of 16384 operations, timed with CUDA
+ * events over the whole GPU.  The rates bound the
+ * page kernels (their roofline); bench.py reports them.  Fills out[0 ..
+ * MS_PIPE_CLASSES - 1] in the order of the enum.  Allocates and frees its
+ * own scratch; takes about a second.
+ */
+enum {
+  MS_PIPE_ADD = 0,      /* add.u32 */
+  MS_PIPE_XOR = 1,      /* xor.b32 (LOP3) */
+  MS_PIPE_SHF = 2,      /* shf.l.wrap.b32 (funnel-shift rotate) */
+  MS_PIPE_PRMT = 3,     /* prmt.b32 (byte permute) */
+  MS_PIPE_MAD = 4,      /* mad.lo.u32 */
+  MS_PIPE_MULHI = 5,    /* mul.hi.u32 */
+  MS_PIPE_XOR_MAD = 6,  /* xor and mad.lo, 1:1 */
+  MS_PIPE_SHF_MAD = 7,  /* shf and mad.lo, 1:1 */
+  MS_PIPE_XOR_ADD = 8,  /* xor and add, 1:1 */
+  MS_PIPE_XOR_SHF = 9,  /* xor and shf, 1:1 */
+  MS_PIPE_CLASSES = 10
+};
+
+typedef struct ms_pipe_rate {
+  int32_t op_class;         /* MS_PIPE_* */
+  int32_t reserved;
+  double lanes_per_sm_clk;  /* tops / (SMs x sm_mhz): lane operations per SM per clock */
+  double sm_mhz;            /* SM clock seen during the run (clock64 vs globaltimer) */
+  double tops;              /* whole-GPU lane operations per second / 1e12 (CUDA events) */
+} ms_pipe_rate;
+
+/* MS_EINVAL: bad device or out == NULL or n_out < MS_PIPE_CLASSES. */
+int ms_probe_int_pipes(int device, ms_pipe_rate *out, size_t n_out);
+
 #ifdef __cplusplus
 }
 #endif

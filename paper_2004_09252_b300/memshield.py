@@ -129,6 +129,14 @@ class ms_window_stats(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("fault_p50_us", "fault_p99_us", "fault_max_us", "elapsed_s")]
 
 
+class ms_pipe_rate(ctypes.Structure):
+    _fields_ = [("op_class", ctypes.c_int32), ("reserved", ctypes.c_int32), ("lanes_per_sm_clk", ctypes.c_double),
+                ("sm_mhz", ctypes.c_double), ("tops", ctypes.c_double)]
+
+
+PIPE_CLASSES = ("add", "xor", "shf", "prmt", "mad", "mulhi", "xor+mad", "shf+mad", "xor+add", "xor+shf")
+
+
 class ms_resident_config(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_uint32), ("ring_entries", ctypes.c_uint32), ("idle_exit_us", ctypes.c_uint32),
                 ("max_run_ms", ctypes.c_uint32)]
@@ -193,6 +201,7 @@ def _load():
         "ms_resident_replay": (I, [P, P, U64, S, P, P, P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.c_uint32]),
         "ms_window_run": (I, [P, ctypes.POINTER(ms_window_config), ctypes.POINTER(ms_window_client), S,
                               ctypes.POINTER(ms_window_stats), P, ctypes.c_uint32]),
+        "ms_probe_int_pipes": (I, [I, ctypes.POINTER(ms_pipe_rate), S]),
         "ms_window_run_resident": (I, [P, P, U64, ctypes.POINTER(ms_window_config), ctypes.POINTER(ms_window_client),
                                        S, ctypes.POINTER(ms_window_stats), P, ctypes.c_uint32]),
         "ms_crypt_pages_dom_dev": (I, [P, P, S]),
@@ -243,6 +252,15 @@ def _ptr(x) -> int:
     if isinstance(x, np.ndarray):
         return x.ctypes.data
     raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def probe_int_pipes(device: int = 0) -> list[dict]:
+    """Sustained lane operations per SM per clock of the cipher's integer op
+    classes on `device` (ms_probe_int_pipes)."""
+    arr = (ms_pipe_rate * len(PIPE_CLASSES))()
+    _check(_lib.ms_probe_int_pipes(device, arr, len(PIPE_CLASSES)), "ms_probe_int_pipes")
+    return [{"class": PIPE_CLASSES[r.op_class], "lanes_per_sm_clk": round(r.lanes_per_sm_clk, 2),
+             "sm_mhz": round(r.sm_mhz, 1), "tops": round(r.tops, 3)} for r in arr]
 
 
 def pages_dom_array(addrs, page_ids, domains) -> np.ndarray:

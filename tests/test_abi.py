@@ -83,6 +83,37 @@ def test_struct_layout_matches_c():
                     m.ms_tune_result.queue_gbs.offset, m.ms_tune_result.tried.offset]
 
 
+def test_every_struct_matches_c_field_by_field():
+    """Every ctypes struct of the binding has the size and the field offsets
+    of its C declaration, and the entry dtypes match ms_page / ms_page_dom."""
+    from paper_2004_09252_b300 import memshield as m
+    structs = [(name, cls) for name, cls in vars(m).items()
+               if name.startswith("ms_") and isinstance(cls, type) and issubclass(cls, ctypes.Structure)]
+    lines = []
+    for name, cls in structs:
+        lines.append(f'printf("%zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({name}, {f}));')
+    want = []
+    for name, cls in structs:
+        want.append(ctypes.sizeof(cls))
+        want += [getattr(cls, f).offset for f, _ in cls._fields_]
+    lines.append('printf("%zu\\n%zu\\n", sizeof(ms_page), sizeof(ms_page_dom));')
+    lines.append('printf("%zu\\n%zu\\n", offsetof(ms_page_dom, page_id), offsetof(ms_page_dom, domain));')
+    want += [m.PAGE_DTYPE.itemsize, m.PAGE_DOM_DTYPE.itemsize, m.PAGE_DOM_DTYPE.fields["page_id"][1],
+             m.PAGE_DOM_DTYPE.fields["domain"][1]]
+    src = ("#include <stdio.h>\n#include <stddef.h>\n#include \"memshield.h\"\nint main(void) {\n"
+           + "\n".join(lines) + "\nreturn 0;\n}\n")
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", INCLUDE, c, "-o", exe])
+        got = [int(v) for v in subprocess.check_output([exe]).split()]
+    assert len(structs) >= 13
+    assert got == want
+
+
 def test_binding_fails_loudly_without_the_library(tmp_path):
     """No CPU fallback: importing the binding where the library is not built
     (and may not be built) raises instead of running anything."""
