@@ -58,7 +58,8 @@ enum ms_status {
   MS_ECUDA = -4,      /* a CUDA runtime call failed (ms_last_cuda_error gives the code) */
   MS_ETIMEDOUT = -5,  /* a bounded wait ran out; the work may still complete later */
   MS_EBUSY = -6,      /* admission refused: queue or staging budget full */
-  MS_ERANGE = -7      /* size beyond a stated maximum */
+  MS_ERANGE = -7,     /* size beyond a stated maximum */
+  MS_ESTARVED = -8    /* a fed kernel waited wait_ms for entries that never came, and left */
 };
 
 enum ms_op { MS_ENCRYPT = 0, MS_DECRYPT = 1 };
@@ -574,6 +575,59 @@ int ms_window_run_resident(ms_resident *res, void *host_base, uint64_t n_pages, 
  */
 #define MS_NOALLOC_MAX_PAGES 16384u
 int ms_crypt_pages_noalloc(ms_ctx *ctx, int op, const ms_page *pages, size_t n);
+
+/*
+ * ---- Fed form: one persistent kernel drains a queue the host is still filling ----
+ *
+ * Sec. 4.4: the GPU module's workers consume queues that host threads keep
+ * filling.  ms_feed_create allocates a device queue of `capacity` entries
+ * and its pinned host copy.  ms_feed_open launches one persistent K2 grid on
+ * the context's stream over the empty queue.  ms_feed_add_requests appends
+ * requests (as ms_batch_add_requests) and, every `chunk` entries, publishes
+ * them: a copy of the new entries, then a copy of the new count, on the
+ * feed's own stream.  The kernel claims only published entries and works
+ * through each claim as it is published.  ms_feed_close publishes the rest
+ * and marks the feed closed; the kernel drains it and exits, and
+ * ms_sync(ctx) waits for that.  A closed feed can be opened again.
+ *
+ * While open, the grid holds every SM.  Bounded: a CTA that waits wait_ms
+ * for entries that are not published leaves and sets a status bit, and the
+ * next ms_sync returns MS_ESTARVED.  A feed holds `capacity` entries in all
+ * (MS_ERANGE beyond); open another for more.  Entries are checked on the
+ * host (MS_EINVAL); pages must not repeat within a feed.  Destroy every feed
+ * before ms_shutdown of its context.
+ */
+typedef struct ms_feed ms_feed;
+
+typedef struct ms_feed_config {
+  uint32_t capacity;  /* entries per feed (default 1 << 20, max MS_BATCH_MAX_CAPACITY) */
+  uint32_t chunk;     /* entries per publication (default 16384, at least 1024) */
+  uint32_t wait_ms;   /* longest wait of the kernel for a publication (default 2000, max 600000) */
+  uint32_t grab;      /* largest claim per atomic; 0 = the context's tuned value */
+} ms_feed_config;
+
+typedef struct ms_feed_stats {
+  uint64_t requests, pages, publications;
+  uint64_t grid;      /* persistent CTAs of the last run */
+  uint64_t runs, closes;
+} ms_feed_stats;
+
+void ms_feed_config_default(ms_feed_config *cfg);
+/* Allocates 2 x 16 B x capacity (pinned + device); launches nothing. */
+int ms_feed_create(ms_ctx *ctx, const ms_feed_config *cfg, ms_feed **out);
+/* Launch the kernel over an empty queue, after the previous run (if any) has
+ * drained (bounded wait).  MS_EBUSY if already open. */
+int ms_feed_open(ms_feed *feed);
+/* Request r is pages[offsets[r] .. offsets[r + 1]); stops at the first request
+ * that fails; *added (may be NULL) receives the number appended.  MS_EINVAL
+ * when the feed is not open.  A run holds `capacity` entries in all. */
+int ms_feed_add_requests(ms_feed *feed, size_t n_requests, const int *ops, const uint64_t *offsets,
+                         const ms_page *pages, size_t *added);
+/* Publish what is left and close; idempotent. */
+int ms_feed_close(ms_feed *feed);
+int ms_feed_get_stats(const ms_feed *feed, ms_feed_stats *out);
+/* Close if open, wait (bounded) for the kernel, free.  NULL is a no-op. */
+int ms_feed_destroy(ms_feed *feed);
 
 /*
  * ---- Measurement: integer pipe rates (the paper has no counterpart) ----

@@ -175,6 +175,7 @@ const char *ms_strerror(int code) {
     case MS_ETIMEDOUT: return "bounded wait timed out";
     case MS_EBUSY: return "busy: admission refused";
     case MS_ERANGE: return "size beyond the stated maximum";
+    case MS_ESTARVED: return "a fed kernel waited for entries that never came";
     default: return "unknown error";
   }
 }
@@ -341,6 +342,14 @@ int ms_crypt_range(ms_ctx *c, int op, void *d_base, uint64_t first_page_id, size
   return e == cudaSuccess ? MS_OK : cuda_fail(c, e);
 }
 
+namespace {
+// The call status for status-word bits: a starved feed first, then a bad entry.
+int status_code(unsigned st) {
+  if (st & kStatusFeedTimeout) return MS_ESTARVED;
+  return (st & kStatusBadEntry) ? MS_EINVAL : MS_OK;
+}
+}  // namespace
+
 int ms_sync(ms_ctx *c) { return c ? ms_sync_for(c, c->cfg.timeout_ms) : MS_ENOTINIT; }
 
 int ms_sync_for(ms_ctx *c, uint32_t timeout_ms) {
@@ -363,7 +372,7 @@ int ms_sync_for(ms_ctx *c, uint32_t timeout_ms) {
     if (rc != MS_OK) return rc;
     const unsigned st = c->status_acc;
     c->status_acc = 0;
-    return (st & kStatusBadEntry) ? MS_EINVAL : MS_OK;
+    return status_code(st);
   }
   // Queue the read and clear of the device status word behind the submitted
   // work and wait once (one round trip).  On a timeout the read stays
@@ -379,7 +388,7 @@ int ms_sync_for(ms_ctx *c, uint32_t timeout_ms) {
   c->status_pending = false;
   const unsigned st = *(volatile unsigned int *)c->h_status | c->status_acc;
   c->status_acc = 0;
-  return (st & kStatusBadEntry) ? MS_EINVAL : MS_OK;
+  return status_code(st);
 }
 
 int ms_shutdown(ms_ctx *c) {

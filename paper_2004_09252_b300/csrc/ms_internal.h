@@ -13,6 +13,9 @@
 
 namespace ms {
 
+// Status-word bits beyond kStatusBadEntry (1).
+constexpr unsigned kStatusFeedTimeout = 2u;  // a fed kernel gave up waiting for entries
+
 // Launch shape of the page kernels; picked by the autotuner or set in ms_config.
 // The default is the fastest shape measured on B300 for the 1 GiB bulk
 // configuration (1852 GB/s): 4 blocks per thread, 128 threads, full unroll,

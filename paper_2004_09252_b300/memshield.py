@@ -19,6 +19,7 @@ MS_PAGE_BYTES = 4096
 MS_BLOCKS_PER_PAGE = 64
 MS_KEY_BYTES = 32
 MS_OK, MS_EINVAL, MS_ENOTINIT, MS_ENOMEM, MS_ECUDA, MS_ETIMEDOUT, MS_EBUSY, MS_ERANGE = 0, -1, -2, -3, -4, -5, -6, -7
+MS_ESTARVED = -8
 MS_ENCRYPT, MS_DECRYPT = 0, 1
 MS_NOALLOC_MAX_PAGES = 16384
 MS_FAULT_LAUNCH, MS_FAULT_COPY, MS_FAULT_GRAPH, MS_FAULT_SERVER = 1, 2, 4, 8
@@ -129,6 +130,15 @@ class ms_window_stats(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("fault_p50_us", "fault_p99_us", "fault_max_us", "elapsed_s")]
 
 
+class ms_feed_config(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_uint32), ("chunk", ctypes.c_uint32), ("wait_ms", ctypes.c_uint32),
+                ("grab", ctypes.c_uint32)]
+
+
+class ms_feed_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("requests", "pages", "publications", "grid", "runs", "closes")]
+
+
 class ms_pipe_rate(ctypes.Structure):
     _fields_ = [("op_class", ctypes.c_int32), ("reserved", ctypes.c_int32), ("lanes_per_sm_clk", ctypes.c_double),
                 ("sm_mhz", ctypes.c_double), ("tops", ctypes.c_double)]
@@ -202,6 +212,13 @@ def _load():
         "ms_window_run": (I, [P, ctypes.POINTER(ms_window_config), ctypes.POINTER(ms_window_client), S,
                               ctypes.POINTER(ms_window_stats), P, ctypes.c_uint32]),
         "ms_probe_int_pipes": (I, [I, ctypes.POINTER(ms_pipe_rate), S]),
+        "ms_feed_config_default": (None, [ctypes.POINTER(ms_feed_config)]),
+        "ms_feed_create": (I, [P, ctypes.POINTER(ms_feed_config), ctypes.POINTER(P)]),
+        "ms_feed_open": (I, [P]),
+        "ms_feed_add_requests": (I, [P, S, P, P, P, ctypes.POINTER(ctypes.c_size_t)]),
+        "ms_feed_close": (I, [P]),
+        "ms_feed_get_stats": (I, [P, ctypes.POINTER(ms_feed_stats)]),
+        "ms_feed_destroy": (I, [P]),
         "ms_window_run_resident": (I, [P, P, U64, ctypes.POINTER(ms_window_config), ctypes.POINTER(ms_window_client),
                                        S, ctypes.POINTER(ms_window_stats), P, ctypes.c_uint32]),
         "ms_crypt_pages_dom_dev": (I, [P, P, S]),
@@ -367,6 +384,9 @@ class Context:
               per_page_domain: bool = False) -> "Batch":
         return Batch(self, capacity, use_graph, grab, ctas_per_sm, per_page_domain)
 
+    def feed(self, capacity: int = 0, chunk: int = 0, wait_ms: int = 0, grab: int = 0) -> "Feed":
+        return Feed(self, capacity, chunk, wait_ms, grab)
+
     def get_shape(self) -> dict:
         sh = ms_shape()
         _check(_lib.ms_get_shape(self.handle, ctypes.byref(sh)), "ms_get_shape")
@@ -409,6 +429,63 @@ class Context:
             self.shutdown()
         except Exception:
             pass
+
+
+class Feed:
+    """An ms_feed: one persistent kernel drains a device queue the host is still
+    filling.  Created closed; open() starts a run, close() ends it."""
+
+    def __init__(self, ctx: Context, capacity: int = 0, chunk: int = 0, wait_ms: int = 0, grab: int = 0):
+        cfg = ms_feed_config()
+        _lib.ms_feed_config_default(ctypes.byref(cfg))
+        if capacity:
+            cfg.capacity = capacity
+        if chunk:
+            cfg.chunk = chunk
+        if wait_ms:
+            cfg.wait_ms = wait_ms
+        cfg.grab = grab
+        h = ctypes.c_void_p()
+        _check(_lib.ms_feed_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "ms_feed_create")
+        self.handle = h.value
+        self.ctx = ctx
+
+    def open(self) -> "Feed":
+        _check(_lib.ms_feed_open(self.handle), "ms_feed_open")
+        return self
+
+    def add_requests(self, ops: np.ndarray, offsets: np.ndarray, pages: np.ndarray, first: int = 0,
+                     count: int | None = None) -> int:
+        """Append requests first..first+count-1 of a request table; returns how many were appended."""
+        ops = np.ascontiguousarray(ops, dtype=np.int32)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        pages = np.ascontiguousarray(pages, dtype=PAGE_DTYPE)
+        n = (len(ops) - first) if count is None else count
+        added = ctypes.c_size_t(0)
+        _check(_lib.ms_feed_add_requests(self.handle, n, ops.ctypes.data + 4 * first, offsets.ctypes.data + 8 * first,
+                                         pages.ctypes.data, ctypes.byref(added)), "ms_feed_add_requests")
+        return added.value
+
+    def close(self) -> None:
+        _check(_lib.ms_feed_close(self.handle), "ms_feed_close")
+
+    def stats(self) -> dict:
+        st = ms_feed_stats()
+        _check(_lib.ms_feed_get_stats(self.handle, ctypes.byref(st)), "ms_feed_get_stats")
+        return {f: getattr(st, f) for f, _ in ms_feed_stats._fields_}
+
+    def destroy(self) -> int:
+        if self.handle:
+            rc = _lib.ms_feed_destroy(self.handle)
+            self.handle = None
+            return rc
+        return MS_OK
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
 
 
 class Batch:
