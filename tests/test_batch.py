@@ -170,11 +170,12 @@ def test_autotune_then_parity_and_table(ms, key1):
 
 
 @pytest.mark.slow
-def test_batching_config_full_size(ms, key1):
+@pytest.mark.parametrize("form", ["batch", "feed"])
+def test_batching_config_full_size(ms, key1, form):
     """The batching configuration at full size: 20,000 Zipf(1.2) requests (1..512
     pages) scattered over an 8 GiB buffer (seed 3).  The persistent batched path
-    and one launch per request give identical 8 GiB buffers; sampled pages match
-    the oracle."""
+    (graph-launched submits, or one fed launch) and one launch per request give
+    identical 8 GiB buffers; sampled pages match the oracle."""
     n_slots = 2097152
     sizes, slots, ops = synth.batching_workload(3)
     base_pages = synth.page_bytes_fast(3, 0, 262144)              # 1 GiB pattern, tiled
@@ -182,7 +183,19 @@ def test_batching_config_full_size(ms, key1):
     a.view(8, -1).copy_(torch.from_numpy(base_pages).cuda().unsqueeze(0).expand(8, -1))
     b = a.clone()
     with make_ctx(ms, key1) as ctx:
-        run_batched(ms, ctx, a, sizes, slots, ops, batch_requests=500)
+        if form == "batch":
+            run_batched(ms, ctx, a, sizes, slots, ops, batch_requests=500)
+        else:
+            offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+            sl = slots.astype(np.uint64)
+            table = ms.pages_array(a.data_ptr() + PAGE * sl, sl)
+            with ctx.feed(capacity=len(slots)) as f:
+                f.open()
+                first = 0
+                while first < len(sizes):
+                    first += f.add_requests(ops.astype(np.int32), offsets, table, first, min(700, len(sizes) - first))
+                f.close()
+                ctx.sync_checked()
         off = 0
         base = b.data_ptr()
         for sz in sizes:
