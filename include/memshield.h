@@ -141,6 +141,26 @@ int ms_crypt_pages_dom(ms_ctx *ctx, const ms_page_dom *pages, size_t n);
 int ms_crypt_pages_dom_dev(ms_ctx *ctx, const ms_page_dom *d_pages, size_t n);
 
 /*
+ * Ticketed submission (per-request completion, the fault path's need): the
+ * host list `pages` (checked and copied as for ms_encrypt_pages; the page
+ * addresses may be device memory or pinned, mapped host memory, which the
+ * kernel then reads and writes in place over the host link) is queued as one
+ * launch on the context's stream, and *ticket names it.  n = 0 gives a ticket
+ * that completes after everything queued before it.  ms_poll: 1 done, 0
+ * pending, < 0 error (MS_EINVAL for a ticket never issued).  ms_wait: MS_OK,
+ * MS_ETIMEDOUT after timeout_ms, or an error.  At most MS_TICKETS
+ * submissions may be pending: a submit whose ring slot still belongs to a
+ * pending ticket returns MS_EBUSY (wait for older tickets first).
+ */
+#define MS_TICKETS 4096
+/* The device address of pinned, mapped host memory (for page entries that the
+ * kernels read and write in place); MS_EINVAL for any other pointer. */
+int ms_host_device_address(const void *host_ptr, uint64_t *dev_addr);
+int ms_submit_host(ms_ctx *ctx, int op, const ms_page *pages, size_t n, uint64_t *ticket);
+int ms_poll(ms_ctx *ctx, uint64_t ticket);
+int ms_wait(ms_ctx *ctx, uint64_t ticket, uint32_t timeout_ms);
+
+/*
  * Contiguous form: n_pages pages back to back at the device address d_base
  * (16-byte aligned); page k has id first_page_id + k.  No entry list is read.
  * MS_EINVAL when the ids would wrap past 2^64 - 1 (a wrapped id would reuse

@@ -87,10 +87,9 @@ void set_list<ms_page>(PageArgs &a, const ms_page *p) { a.pages = p; }
 template <>
 void set_list<ms_page_dom>(PageArgs &a, const ms_page_dom *p) { a.dpages = p; }
 
+// Host-side entry checks of a host list (addresses; duplicates if configured).
 template <typename E>
-int submit_list_host(ms_ctx *c, const E *pages, size_t n) {
-  if (!c || !c->alive) return MS_ENOTINIT;
-  if (n == 0) return MS_OK;
+int check_list_host(const ms_ctx *c, const E *pages, size_t n) {
   if (!pages) return MS_EINVAL;
   for (size_t i = 0; i < n; ++i)
     if (pages[i].addr == 0 || (pages[i].addr & 15u)) return MS_EINVAL;
@@ -100,7 +99,25 @@ int submit_list_host(ms_ctx *c, const E *pages, size_t n) {
     for (size_t i = 0; i < n; ++i)
       if (!seen.insert(pages[i].addr).second) return MS_EINVAL;
   }
+  return MS_OK;
+}
+
+// Queue a checked host list on the context stream; the caller holds c->mu.
+template <typename E>
+int submit_list_host_locked(ms_ctx *c, const E *pages, size_t n);
+
+template <typename E>
+int submit_list_host(ms_ctx *c, const E *pages, size_t n) {
+  if (!c || !c->alive) return MS_ENOTINIT;
+  if (n == 0) return MS_OK;
+  const int rc = check_list_host(c, pages, n);
+  if (rc != MS_OK) return rc;
   std::lock_guard<std::mutex> lk(c->mu);
+  return submit_list_host_locked(c, pages, n);
+}
+
+template <typename E>
+int submit_list_host_locked(ms_ctx *c, const E *pages, size_t n) {
   DeviceGuard g(c->device);
   // A short list goes in the kernel parameters: one launch, no copies.  A
   // shape the caller chose is kept, so such contexts take the staged path.
@@ -203,6 +220,8 @@ static void release(ms_ctx *c) {
     if (c->hs[i]) cudaStreamDestroy(c->hs[i]);
     if (c->hs_buf[i]) cudaFree(c->hs_buf[i]);
   }
+  for (cudaEvent_t &ev : c->tk_ev)
+    if (ev) cudaEventDestroy(ev);
   if (c->sync_ev) cudaEventDestroy(c->sync_ev);
   if (c->status_ev) cudaEventDestroy(c->status_ev);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -351,6 +370,76 @@ int status_code(unsigned st) {
 }  // namespace
 
 int ms_sync(ms_ctx *c) { return c ? ms_sync_for(c, c->cfg.timeout_ms) : MS_ENOTINIT; }
+
+// ---------------------------------------------------------------- tickets
+int ms_submit_host(ms_ctx *c, int op, const ms_page *pages, size_t n, uint64_t *ticket) {
+  if (!c || !c->alive) return MS_ENOTINIT;
+  if (!ticket || (op != MS_ENCRYPT && op != MS_DECRYPT)) return MS_EINVAL;
+  if (n) {
+    const int rc = check_list_host(c, pages, n);
+    if (rc != MS_OK) return rc;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  const uint64_t t = c->tk_next;
+  cudaEvent_t &ev = c->tk_ev[t % kTickets];
+  if (!ev) {
+    const cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+  } else {
+    // the slot's previous ticket (t - kTickets) must have finished before its event is reused
+    const cudaError_t q = cudaEventQuery(ev);
+    if (q == cudaErrorNotReady) return MS_EBUSY;
+    if (q != cudaSuccess) return cuda_fail(c, q);
+  }
+  if (n) {
+    const int rc = submit_list_host_locked(c, pages, n);
+    if (rc != MS_OK) return rc;
+  }
+  const cudaError_t e = cudaEventRecord(ev, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e);
+  c->tk_next = t + 1;
+  *ticket = t;
+  return MS_OK;
+}
+
+int ms_host_device_address(const void *host_ptr, uint64_t *dev_addr) {
+  if (!host_ptr || !dev_addr) return MS_EINVAL;
+  void *dp = nullptr;
+  if (cudaHostGetDevicePointer(&dp, const_cast<void *>(host_ptr), 0) != cudaSuccess || !dp) {
+    cudaGetLastError();
+    return MS_EINVAL;  // not pinned, mapped host memory
+  }
+  *dev_addr = (uint64_t)dp;
+  return MS_OK;
+}
+
+int ms_poll(ms_ctx *c, uint64_t ticket) {
+  if (!c || !c->alive) return MS_ENOTINIT;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (ticket >= c->tk_next) return MS_EINVAL;
+  if (c->tk_next - ticket > kTickets) return 1;  // its slot was reused, which needs it finished
+  DeviceGuard g(c->device);
+  const cudaError_t q = cudaEventQuery(c->tk_ev[ticket % kTickets]);
+  if (q == cudaSuccess) return 1;
+  if (q == cudaErrorNotReady) return 0;
+  return cuda_fail(c, q);
+}
+
+int ms_wait(ms_ctx *c, uint64_t ticket, uint32_t timeout_ms) {
+  using clk = std::chrono::steady_clock;
+  const auto t0 = clk::now();
+  for (int it = 0;; ++it) {
+    const int p = ms_poll(c, ticket);
+    if (p != 0) return p == 1 ? MS_OK : p;
+    const auto el = clk::now() - t0;
+    if (el > std::chrono::milliseconds(timeout_ms)) return MS_ETIMEDOUT;
+    if (el > std::chrono::microseconds(50)) {
+      struct timespec ts = {0, 5000};
+      nanosleep(&ts, nullptr);
+    }
+  }
+}
 
 int ms_sync_for(ms_ctx *c, uint32_t timeout_ms) {
   if (!c || !c->alive) return MS_ENOTINIT;

@@ -36,6 +36,7 @@ struct QTune {
 };
 
 constexpr int kListSlots = 4;
+constexpr int kTickets = MS_TICKETS;  // completion events of ms_submit_host, reused in a ring
 constexpr int kMaxHostStreams = 4;
 
 struct ListSlot {
@@ -70,6 +71,8 @@ struct ms_ctx {
   std::atomic<unsigned> tune_gen{0};  // bumped whenever tune/qtune change
   ms::ListSlot slots[ms::kListSlots];
   int next_slot = 0;
+  cudaEvent_t tk_ev[ms::kTickets] = {};  // created on first use
+  uint64_t tk_next = 0;                  // the next ticket
   // host streaming (ms_crypt_host)
   cudaStream_t hs[ms::kMaxHostStreams] = {};
   cudaEvent_t hs_ev[ms::kMaxHostStreams] = {};

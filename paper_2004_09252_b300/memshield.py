@@ -212,6 +212,10 @@ def _load():
         "ms_window_run": (I, [P, ctypes.POINTER(ms_window_config), ctypes.POINTER(ms_window_client), S,
                               ctypes.POINTER(ms_window_stats), P, ctypes.c_uint32]),
         "ms_probe_int_pipes": (I, [I, ctypes.POINTER(ms_pipe_rate), S]),
+        "ms_submit_host": (I, [P, I, P, S, ctypes.POINTER(U64)]),
+        "ms_poll": (I, [P, U64]),
+        "ms_wait": (I, [P, U64, ctypes.c_uint32]),
+        "ms_host_device_address": (I, [P, ctypes.POINTER(U64)]),
         "ms_feed_config_default": (None, [ctypes.POINTER(ms_feed_config)]),
         "ms_feed_create": (I, [P, ctypes.POINTER(ms_feed_config), ctypes.POINTER(P)]),
         "ms_feed_open": (I, [P]),
@@ -269,6 +273,13 @@ def _ptr(x) -> int:
     if isinstance(x, np.ndarray):
         return x.ctypes.data
     raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def host_device_address(host_base) -> int:
+    """Device address of pinned, mapped host memory (ms_host_device_address)."""
+    a = ctypes.c_uint64()
+    _check(_lib.ms_host_device_address(_ptr(host_base), ctypes.byref(a)), "ms_host_device_address")
+    return a.value
 
 
 def probe_int_pipes(device: int = 0) -> list[dict]:
@@ -383,6 +394,20 @@ class Context:
     def batch(self, capacity: int = 0, use_graph: bool = True, grab: int = 0, ctas_per_sm: int = 0,
               per_page_domain: bool = False) -> "Batch":
         return Batch(self, capacity, use_graph, grab, ctas_per_sm, per_page_domain)
+
+    def submit_host(self, op: int, pages: np.ndarray) -> int:
+        """Queue one host list; returns its ticket (ms_submit_host)."""
+        pages = np.ascontiguousarray(pages, dtype=PAGE_DTYPE)
+        t = ctypes.c_uint64()
+        _check(_lib.ms_submit_host(self.handle, op, pages.ctypes.data, pages.size, ctypes.byref(t)), "ms_submit_host")
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        """1 done, 0 pending, < 0 an error code."""
+        return _lib.ms_poll(self.handle, ticket)
+
+    def wait(self, ticket: int, timeout_ms: int = 10000) -> None:
+        _check(_lib.ms_wait(self.handle, ticket, timeout_ms), "ms_wait")
 
     def feed(self, capacity: int = 0, chunk: int = 0, wait_ms: int = 0, grab: int = 0) -> "Feed":
         return Feed(self, capacity, chunk, wait_ms, grab)

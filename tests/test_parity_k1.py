@@ -353,3 +353,32 @@ def test_random_key_from_the_os(ms):
             assert np.array_equal(d.cpu().numpy(), plain)
     assert not np.array_equal(outs[0], outs[1])
     assert not np.array_equal(outs[0], plain)
+
+
+def test_ticketed_submissions(ms, key1):
+    """ms_submit_host / ms_poll / ms_wait: per-submission completion, on device
+    pages and on pinned host pages the kernel works on in place."""
+    n = 600
+    plain = synth.page_bytes(175, 0, n)
+    d = dev(plain)
+    h = torch.from_numpy(plain.copy()).pin_memory()
+    hbase = ms.host_device_address(h)
+    with ms.Context(key1) as ctx:
+        tickets = []
+        for lo in range(0, n, 100):                     # six requests of 100 pages, each side
+            ids = np.arange(lo, lo + 100, dtype=np.uint64)
+            tickets.append(ctx.submit_host(ms.MS_ENCRYPT, ms.pages_array(d.data_ptr() + PAGE * ids, ids)))
+            tickets.append(ctx.submit_host(ms.MS_ENCRYPT, ms.pages_array(hbase + PAGE * ids, ids)))
+        assert tickets == list(range(tickets[0], tickets[0] + len(tickets)))
+        for t in tickets:
+            ctx.wait(t, 10000)
+            assert ctx.poll(t) == 1
+        marker = ctx.submit_host(ms.MS_ENCRYPT, ms.pages_array([], []))   # empty: completes after the rest
+        ctx.wait(marker)
+        assert ctx.poll(marker + 1) == ms.MS_EINVAL                        # never issued
+        with pytest.raises(ms.MemShieldError):
+            ms.host_device_address(d)                                       # device memory is not host memory
+    all_ = np.arange(n, dtype=np.uint64)
+    want = oracle_expected(key1, plain, all_, all_)
+    assert np.array_equal(d.cpu().numpy(), want)
+    assert np.array_equal(h.numpy(), want)
