@@ -450,6 +450,20 @@ def run_small(args):
                      "device_us_p99": round(float(np.percentile(dev_us, 99)), 2),
                      "call_to_sync_us_p50": round(float(np.percentile(wall_us, 50)), 2),
                      "call_to_sync_us_p99": round(float(np.percentile(wall_us, 99)), 2)}
+    # one page per request, waited for on its own ticket (the fault path), on a
+    # device page and on a pinned host page the kernel works on in place
+    hpg = torch.empty(PAGE * 2, dtype=torch.uint8).pin_memory()
+    one = {"device_page": ms.pages_array([d.data_ptr()], [0]),
+           "pinned_host_page": ms.pages_array([ms.host_device_address(hpg)], [0])}
+    for name, entry in one.items():
+        lat = []
+        for i in range(args.warmup + 2 * args.steps):
+            t0 = time.perf_counter()
+            ctx.wait(ctx.submit_host(i % 2, entry))
+            if i >= args.warmup:
+                lat.append((time.perf_counter() - t0) * 1e6)
+        out[f"ticket_{name}"] = {"submit_to_done_us_p50": round(float(np.percentile(lat, 50)), 2),
+                                 "submit_to_done_us_p99": round(float(np.percentile(lat, 99)), 2)}
     ok = torch.equal(d, plain)  # an even number of launches in every form
     ctx.encrypt_pages(table)
     ctx.sync_checked()
