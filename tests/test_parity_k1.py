@@ -382,3 +382,40 @@ def test_ticketed_submissions(ms, key1):
     want = oracle_expected(key1, plain, all_, all_)
     assert np.array_equal(d.cpu().numpy(), want)
     assert np.array_equal(h.numpy(), want)
+
+
+def test_concurrent_submitters_on_one_context(ms, key1):
+    """Four host threads submit and wait on one context at once (the paper's
+    many clients feeding one GPU module): every thread's pages end as the
+    oracle says, and every ticket completes."""
+    import threading
+    n_threads, per, reqs = 4, 800, 200
+    n = n_threads * per
+    plain = synth.page_bytes_fast(177, 0, n)
+    d = dev(plain)
+    torch.cuda.synchronize()
+    errors = []
+    with ms.Context(key1) as ctx:
+        def client(k):
+            try:
+                rng_sizes = (synth.splitmix64(178 + k, 0, reqs) % np.uint64(4) + np.uint64(1)).astype(int)
+                pages = synth.scattered_slots(190 + k, per, int(rng_sizes.sum())).astype(np.uint64) + np.uint64(k * per)
+                off = 0
+                for sz in rng_sizes:
+                    sl = pages[off:off + sz]
+                    t = ctx.submit_host(ms.MS_ENCRYPT, ms.pages_array(d.data_ptr() + PAGE * sl, sl))
+                    ctx.wait(t, 10000)
+                    off += sz
+                rest = np.setdiff1d(np.arange(k * per, (k + 1) * per, dtype=np.uint64), pages)
+                ctx.encrypt_pages(ms.pages_array(d.data_ptr() + PAGE * rest, rest))   # the rest, untracked
+            except Exception as e:  # surfaced below
+                errors.append(e)
+        th = [threading.Thread(target=client, args=(k,)) for k in range(n_threads)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        ctx.sync_checked()
+    assert not errors, errors
+    all_ = np.arange(n, dtype=np.uint64)
+    assert np.array_equal(d.cpu().numpy(), oracle_expected(key1, plain, all_, all_))
