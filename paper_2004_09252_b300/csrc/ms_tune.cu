@@ -119,7 +119,7 @@ int ms_autotune(ms_ctx *c, size_t sample_pages, ms_tune_result *out) {
       PageArgs a = make_args(c);
       a.base = x.pages;
       a.n_pages = sample_pages;
-      float ms;
+      float ms = 0.0f;
       e = time_median(s, x, [&] { return launch_pages_shape(a, rounds, t, true, s); }, &ms);
       if (e != cudaSuccess) return cuda_fail(c, e);
       r.tried += 1;
@@ -161,7 +161,7 @@ int ms_autotune(ms_ctx *c, size_t sample_pages, ms_tune_result *out) {
       q.mc.m12 = 1u << 12;
       q.mc.m7 = 1u << 7;
       const int grid = queue_grid(c, k, best.tpc, cps);
-      float ms;
+      float ms = 0.0f;
       e = time_median(s, x, [&] {
         cudaError_t e1 = cudaMemsetAsync(x.hdr + 1, 0, sizeof(uint32_t), s);
         return e1 == cudaSuccess ? k.launch(q, grid, best.tpc, s) : e1;
