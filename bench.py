@@ -457,10 +457,10 @@ def run_small(args):
            "pinned_host_page": ms.pages_array([ms.host_device_address(hpg)], [0])}
     for name, entry in one.items():
         lat = []
-        for i in range(args.warmup + 2 * args.steps):
+        for i in range(2 * (args.warmup + args.steps)):  # an even count: the page ends as it started
             t0 = time.perf_counter()
             ctx.wait(ctx.submit_host(i % 2, entry))
-            if i >= args.warmup:
+            if i >= 2 * args.warmup:
                 lat.append((time.perf_counter() - t0) * 1e6)
         out[f"ticket_{name}"] = {"submit_to_done_us_p50": round(float(np.percentile(lat, 50)), 2),
                                  "submit_to_done_us_p99": round(float(np.percentile(lat, 99)), 2)}
