@@ -381,7 +381,7 @@ int ms_submit_host(ms_ctx *c, int op, const ms_page *pages, size_t n, uint64_t *
   }
   std::lock_guard<std::mutex> lk(c->mu);
   DeviceGuard g(c->device);
-  const uint64_t t = c->tk_next;
+  const uint64_t t = c->tk_next.load();
   cudaEvent_t &ev = c->tk_ev[t % kTickets];
   if (!ev) {
     const cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -398,7 +398,7 @@ int ms_submit_host(ms_ctx *c, int op, const ms_page *pages, size_t n, uint64_t *
   }
   const cudaError_t e = cudaEventRecord(ev, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);
-  c->tk_next = t + 1;
+  c->tk_next.store(t + 1, std::memory_order_release);  // the event exists and is recorded
   *ticket = t;
   return MS_OK;
 }
@@ -414,11 +414,15 @@ int ms_host_device_address(const void *host_ptr, uint64_t *dev_addr) {
   return MS_OK;
 }
 
+// Lock-free, so that a client waiting on its ticket is not held up by
+// another thread's ms_sync.  A newer ticket may re-record the slot's event
+// after the distance check; that happens only once the old ticket has
+// finished, and then reads as pending once, until the distance check says done.
 int ms_poll(ms_ctx *c, uint64_t ticket) {
   if (!c || !c->alive) return MS_ENOTINIT;
-  std::lock_guard<std::mutex> lk(c->mu);
-  if (ticket >= c->tk_next) return MS_EINVAL;
-  if (c->tk_next - ticket > kTickets) return 1;  // its slot was reused, which needs it finished
+  const uint64_t next = c->tk_next.load(std::memory_order_acquire);
+  if (ticket >= next) return MS_EINVAL;
+  if (next - ticket > kTickets) return 1;  // its slot was reused, which needs it finished
   DeviceGuard g(c->device);
   const cudaError_t q = cudaEventQuery(c->tk_ev[ticket % kTickets]);
   if (q == cudaSuccess) return 1;

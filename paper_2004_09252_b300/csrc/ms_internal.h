@@ -72,7 +72,7 @@ struct ms_ctx {
   ms::ListSlot slots[ms::kListSlots];
   int next_slot = 0;
   cudaEvent_t tk_ev[ms::kTickets] = {};  // created on first use
-  uint64_t tk_next = 0;                  // the next ticket
+  std::atomic<uint64_t> tk_next{0};      // the next ticket (read without the lock by ms_poll)
   // host streaming (ms_crypt_host)
   cudaStream_t hs[ms::kMaxHostStreams] = {};
   cudaEvent_t hs_ev[ms::kMaxHostStreams] = {};

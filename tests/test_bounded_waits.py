@@ -59,3 +59,31 @@ def test_server_wait_times_out(ms, key1):
         assert rc in (ms.MS_OK, ms.MS_ETIMEDOUT)
         srv.wait(t, 10000)
         assert srv.poll(t) == 1
+
+
+def test_ticket_wait_is_not_held_up_by_a_sync(ms, key1):
+    """A client waiting on its own ticket is not blocked by another thread's
+    ms_sync that waits for later work (ms_poll takes no lock)."""
+    import threading
+    import time
+    n_big = 262144
+    big = torch.zeros(n_big * PAGE, dtype=torch.uint8, device="cuda")
+    small = torch.zeros(4 * PAGE, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    ids = np.arange(4, dtype=np.uint64)
+    with ms.Context(key1) as ctx:
+        t = ctx.submit_host(ms.MS_ENCRYPT, ms.pages_array(small.data_ptr() + PAGE * ids, ids))
+        for _ in range(40):                                   # ~25 ms of later work
+            ctx.crypt_range(ms.MS_ENCRYPT, big, 0, n_big)
+        done = {}
+        def syncer():
+            done["sync_rc"] = ctx.sync_for(60000)
+            done["sync_t"] = time.perf_counter()
+        th = threading.Thread(target=syncer)
+        th.start()
+        time.sleep(0.002)                                     # the sync now holds the context lock
+        ctx.wait(t, 60000)
+        t_ticket = time.perf_counter()
+        th.join()
+        assert done["sync_rc"] == ms.MS_OK
+        assert t_ticket < done["sync_t"]
