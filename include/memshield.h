@@ -172,7 +172,10 @@ int ms_crypt_range(ms_ctx *ctx, int op, void *d_base, uint64_t first_page_id, si
  * Wait, at most cfg.timeout_ms, until all work submitted on this context has
  * finished.  Returns MS_ETIMEDOUT if the bound ran out (the work is still
  * queued; call again), MS_EINVAL if a device-checked entry was bad since the
- * last ms_sync, MS_ECUDA on a CUDA error.
+ * last ms_sync, MS_ESTARVED if a fed kernel gave up waiting, MS_ECUDA on a
+ * CUDA error.  The context is held for the duration of the wait: other
+ * threads' submissions on it wait too.  Threads that need completion of
+ * their own requests without that use ms_submit_host and ms_wait.
  */
 int ms_sync(ms_ctx *ctx);
 /* ms_sync with its own bound instead of cfg.timeout_ms (0 = only check). */
