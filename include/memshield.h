@@ -570,6 +570,17 @@ int ms_resident_replay(ms_resident *res, void *host_base, uint64_t n_pages, size
 int ms_window_run_resident(ms_resident *res, void *host_base, uint64_t n_pages, const ms_window_config *cfg,
                            const ms_window_client *clients, size_t n_clients, ms_window_stats *stats_out,
                            uint64_t *final_window_out, uint32_t timeout_ms);
+/*
+ * The same clients served by ticketed launches on one context
+ * (ms_submit_host + ms_wait): a fault is one launch waited for, an eviction
+ * one launch not waited for, in place on the pinned, mapped working set.  The
+ * context's stream runs them in submission order, so a fault on a page whose
+ * eviction is still queued runs after it.  The nonce's domain is the
+ * context's: every client's domain must equal it (MS_EINVAL otherwise).
+ */
+int ms_window_run_ticketed(ms_ctx *ctx, void *host_base, uint64_t n_pages, const ms_window_config *cfg,
+                           const ms_window_client *clients, size_t n_clients, ms_window_stats *stats_out,
+                           uint64_t *final_window_out, uint32_t timeout_ms);
 
 /*
  * Allocation-free variant of ms_encrypt_pages / ms_decrypt_pages.  The paper

@@ -122,6 +122,43 @@ struct ResidentBackend {
   }
 };
 
+// One launch per request on a context, each with its own ticket (in place on
+// the pinned working set).  The context's stream runs requests in submission
+// order, so a fault on a page whose eviction is still queued runs after it.
+struct TicketBackend {
+  ms_ctx *ctx;
+  uint64_t dbase;
+  uint32_t timeout_ms;
+  uint64_t last_evict = ~0ull;  // the client's latest eviction ticket
+  std::vector<ms_page> ent;
+  int submit(const uint64_t *pages, size_t k, uint64_t *ticket, int op) {
+    ent.resize(k);
+    for (size_t i = 0; i < k; ++i) {
+      ent[i].addr = dbase + pages[i] * MS_PAGE_BYTES;
+      ent[i].page_id = pages[i];
+    }
+    const auto limit = clk::now() + std::chrono::milliseconds(timeout_ms);
+    for (;;) {
+      const int rc = ms_submit_host(ctx, op, ent.data(), k, ticket);
+      if (rc != MS_EBUSY) return rc;
+      if (clk::now() > limit) return MS_ETIMEDOUT;
+      std::this_thread::yield();
+    }
+  }
+  int fault(uint32_t, uint64_t pg) {
+    uint64_t t;
+    const int rc = submit(&pg, 1, &t, MS_DECRYPT);
+    return rc == MS_OK ? ms_wait(ctx, t, timeout_ms) : rc;
+  }
+  int evict(uint32_t, const uint64_t *pages, size_t k) {
+    uint64_t t;
+    const int rc = submit(pages, k, &t, MS_ENCRYPT);
+    if (rc == MS_OK) last_evict = t;
+    return rc;
+  }
+  int drain() { return last_evict == ~0ull ? MS_OK : ms_wait(ctx, last_evict, timeout_ms); }
+};
+
 template <typename Backend>
 void run_client(Backend &be, const ms_window_config &cfg, ClientRun &cr) {
   const ms_window_client &cl = *cr.cl;
@@ -262,5 +299,20 @@ extern "C" int ms_window_run_resident(ms_resident *res, void *host_base, uint64_
     ResidentBackend be{res, (uint64_t)dbase, cl.first_page, timeout_ms, {}, {}};
     be.last_ticket.assign(cl.n_pages, ~0ull);
     return be;
+  });
+}
+
+extern "C" int ms_window_run_ticketed(ms_ctx *ctx, void *host_base, uint64_t n_pages, const ms_window_config *cfg,
+                                      const ms_window_client *clients, size_t n_clients, ms_window_stats *stats_out,
+                                      uint64_t *final_window_out, uint32_t timeout_ms) {
+  if (!ctx || !host_base || n_pages == 0) return MS_EINVAL;
+  const int rc = check_window_args(cfg, clients, n_clients, n_pages);
+  if (rc != MS_OK) return rc;
+  for (size_t c = 0; c < n_clients; ++c)
+    if (clients[c].domain != ctx->cfg.domain) return MS_EINVAL;  // one context, one domain
+  uint64_t dbase = 0;
+  if (ms_host_device_address(host_base, &dbase) != MS_OK) return MS_EINVAL;
+  return run_clients(*cfg, clients, n_clients, stats_out, final_window_out, [&](const ms_window_client &) {
+    return TicketBackend{ctx, dbase, timeout_ms, ~0ull, {}};
   });
 }

@@ -223,6 +223,8 @@ def _load():
         "ms_feed_close": (I, [P]),
         "ms_feed_get_stats": (I, [P, ctypes.POINTER(ms_feed_stats)]),
         "ms_feed_destroy": (I, [P]),
+        "ms_window_run_ticketed": (I, [P, P, U64, ctypes.POINTER(ms_window_config), ctypes.POINTER(ms_window_client),
+                                       S, ctypes.POINTER(ms_window_stats), P, ctypes.c_uint32]),
         "ms_window_run_resident": (I, [P, P, U64, ctypes.POINTER(ms_window_config), ctypes.POINTER(ms_window_client),
                                        S, ctypes.POINTER(ms_window_stats), P, ctypes.c_uint32]),
         "ms_crypt_pages_dom_dev": (I, [P, P, S]),
@@ -408,6 +410,16 @@ class Context:
 
     def wait(self, ticket: int, timeout_ms: int = 10000) -> None:
         _check(_lib.ms_wait(self.handle, ticket, timeout_ms), "ms_wait")
+
+    def run_window_clients(self, host_base, n_pages: int, window_pages: int, evict_batch: int, clients,
+                           timeout_ms: int = 60000):
+        """Sliding-window clients served by ticketed launches on this context, in
+        place on a pinned, mapped working set (every client's domain must be the
+        context's)."""
+        base = _ptr(host_base)
+        return _run_window(lambda cfg, arr, n, st, fw: _lib.ms_window_run_ticketed(
+            self.handle, base, n_pages, cfg, arr, n, st, fw, timeout_ms),
+            "ms_window_run_ticketed", window_pages, evict_batch, clients)
 
     def feed(self, capacity: int = 0, chunk: int = 0, wait_ms: int = 0, grab: int = 0) -> "Feed":
         return Feed(self, capacity, chunk, wait_ms, grab)

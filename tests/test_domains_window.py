@@ -141,6 +141,33 @@ def test_sliding_window_clients_on_resident_workers(ms, key1, window, batch):
             res.run_window_clients(h, n, 4, 1, [(1, n - 4, 8, np.zeros(2, dtype=np.uint64))])
 
 
+@pytest.mark.parametrize("window,batch", [(4, 1), (16, 9)])
+def test_sliding_window_clients_on_ticketed_launches(ms, key1, window, batch):
+    """The same clients served by one ticketed launch per fault and per eviction
+    on a context (domain 77, shared by every client): the same final state."""
+    per, n_clients = 128, 3
+    n = per * n_clients
+    plain = synth.page_bytes_fast(296, 0, n)
+    h = torch.from_numpy(plain.copy()).pin_memory()
+    dom = 77
+    clients = [(dom, c * per, per, synth.window_trace(297 + c, per, 1500)) for c in range(n_clients)]
+    with ms.Context(key1, domain=dom) as ctx:
+        base = ms.host_device_address(h)
+        ids = np.arange(n, dtype=np.uint64)
+        ctx.wait(ctx.submit_host(ms.MS_ENCRYPT, ms.pages_array(base + PAGE * ids, ids)))   # all start encrypted
+        stats, wins = ctx.run_window_clients(h, n, window, batch, clients)
+        with pytest.raises(ms.MemShieldError):                 # a client with another domain
+            ctx.run_window_clients(h, n, window, batch, [(dom + 1, 0, per, clients[0][3])])
+    ws = h.numpy()
+    for c in range(n_clients):
+        st, win = stats[c], wins[c]
+        assert st["accesses"] == 1500 and st["faults"] - st["evictions"] == len(win) <= window
+        enc = np.array(sorted(set(range(c * per, (c + 1) * per)) - set(win)), dtype=np.uint64)
+        want = plain[c * per * PAGE:(c + 1) * per * PAGE].copy()
+        oracle.crypt_pages(key1, want, enc - np.uint64(c * per), enc, domain=dom)
+        assert np.array_equal(ws[c * per * PAGE:(c + 1) * per * PAGE], want), f"client {c}"
+
+
 def test_window_rejects_bad_configs(ms, key1):
     n = 64
     h = torch.zeros(n * PAGE, dtype=torch.uint8).pin_memory()
