@@ -776,8 +776,6 @@ def run_window(args):
     rows = []
     srv = ms.Server(ctx, ws, n)
     res = ms.Resident(ctx, workers=args.resident_workers) if "resident" in args.window_backends else None
-    # ticketed launches use one context per domain, so their clients share the first client's domain
-    tctx = ms.Context(key, domain=1000) if "ticketed" in args.window_backends else None
     try:
         for c in range(max_clients):           # client pages start encrypted with the client's PID
             for p0 in range(c * per, (c + 1) * per, 4096):
@@ -797,34 +795,14 @@ def run_window(args):
                                 srv.wait(srv.submit(ms.MS_ENCRYPT, np.array(win), domain=1000 + c), 20000)
                         state = {}
                         cl = [(1000 + c, c * per, per, traces[c]) for c in range(n_cl)]
-                        if backend == "ticketed":
-                            # re-key the clients' pages to domain 1000 (decrypt under their own PIDs,
-                            # encrypt under 1000), run, and key them back afterwards
-                            for c in range(1, n_cl):
-                                pg = np.arange(c * per, (c + 1) * per)
-                                for p0 in range(0, per, 4096):
-                                    srv.wait(srv.submit(ms.MS_DECRYPT, pg[p0:p0 + 4096], domain=1000 + c), 20000)
-                                    srv.wait(srv.submit(ms.MS_ENCRYPT, pg[p0:p0 + 4096], domain=1000), 20000)
-                            cl = [(1000, c * per, per, traces[c]) for c in range(n_cl)]
                         t0 = time.perf_counter()
-                        if backend == "ticketed":
-                            st, wins = tctx.run_window_clients(ws, n, wnd, batch, cl, timeout_ms=20000)
+                        if backend == "ticketed":   # one clone of ctx per client: its PID, its stream
+                            st, wins = ctx.run_window_clients(ws, n, wnd, batch, cl, timeout_ms=20000)
                         elif backend == "resident":
                             st, wins = res.run_window_clients(ws, n, wnd, batch, cl, timeout_ms=20000)
                         else:
                             st, wins = srv.run_window_clients(wnd, batch, cl, timeout_ms=20000)
                         el = time.perf_counter() - t0
-                        if backend == "ticketed":
-                            # close the windows under domain 1000 and key the pages back to their PIDs
-                            for c in range(n_cl):
-                                if wins[c]:
-                                    srv.wait(srv.submit(ms.MS_ENCRYPT, np.array(wins[c]), domain=1000), 20000)
-                            for c in range(1, n_cl):
-                                pg = np.arange(c * per, (c + 1) * per)
-                                for p0 in range(0, per, 4096):
-                                    srv.wait(srv.submit(ms.MS_DECRYPT, pg[p0:p0 + 4096], domain=1000), 20000)
-                                    srv.wait(srv.submit(ms.MS_ENCRYPT, pg[p0:p0 + 4096], domain=1000 + c), 20000)
-                            wins = [[] for _ in range(n_cl)]
                         state = {c: wins[c] for c in range(n_cl)}
                         faults = sum(x["faults"] for x in st)
                         rows.append({"backend": backend, "clients": n_cl, "window_pages": wnd, "evict_batch": batch,
@@ -840,8 +818,6 @@ def run_window(args):
         if res is not None:
             res.destroy()
         srv.destroy()
-        if tctx is not None:
-            tctx.shutdown()
     ctx.shutdown()
     print(json.dumps({
         "metric": "sliding-window fault service (faults/s, fault latency)", "unit": "faults/s",

@@ -109,6 +109,15 @@ void ms_config_default(ms_config *cfg);
 int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg);
 
 /*
+ * A context with the same key as `ctx` (copied device to device: the key
+ * never returns to host memory), the given domain (the nonce's PID word),
+ * its own stream and staging, and ctx's launch shape and tuning.  For a
+ * server with many clients: one clone per client PID, each with its own
+ * stream.  Shut it down like any context.
+ */
+int ms_clone(ms_ctx *ctx, uint32_t domain, ms_ctx **out);
+
+/*
  * Encrypt / decrypt (the same transform, Sec. 4.4) n pages listed in HOST
  * memory.  Every entry is checked first (addr != 0, addr % 16 == 0); one bad
  * entry fails the whole call with MS_EINVAL and launches nothing.  The list is
@@ -571,12 +580,12 @@ int ms_window_run_resident(ms_resident *res, void *host_base, uint64_t n_pages, 
                            const ms_window_client *clients, size_t n_clients, ms_window_stats *stats_out,
                            uint64_t *final_window_out, uint32_t timeout_ms);
 /*
- * The same clients served by ticketed launches on one context
- * (ms_submit_host + ms_wait): a fault is one launch waited for, an eviction
- * one launch not waited for, in place on the pinned, mapped working set.  The
- * context's stream runs them in submission order, so a fault on a page whose
- * eviction is still queued runs after it.  The nonce's domain is the
- * context's: every client's domain must equal it (MS_EINVAL otherwise).
+ * The same clients served by ticketed launches (ms_submit_host + ms_wait):
+ * each client gets a clone of ctx (ms_clone) with its own domain and stream;
+ * a fault is one launch waited for, an eviction one launch not waited for,
+ * in place on the pinned, mapped working set.  A client's stream runs its
+ * requests in submission order, so a fault on a page whose eviction is still
+ * queued runs after it.
  */
 int ms_window_run_ticketed(ms_ctx *ctx, void *host_base, uint64_t n_pages, const ms_window_config *cfg,
                            const ms_window_client *clients, size_t n_clients, ms_window_stats *stats_out,

@@ -231,7 +231,11 @@ static void release(ms_ctx *c) {
   delete c;
 }
 
-int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg_in) {
+namespace {
+
+// Context creation; the key comes from host memory (key, NULL = the OS
+// CSPRNG) or, for a clone, from another context's device copy (key_dev).
+int init_ctx(ms_ctx **out, const uint8_t *key, const uint4 *key_dev, const ms_config *cfg_in) {
   if (!out) return MS_EINVAL;
   *out = nullptr;
   ms_config cfg;
@@ -287,9 +291,20 @@ int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg_in) {
   // the GPU and purged from host memory).  The pinned bounce buffer is the
   // only host copy the library makes; it is wiped before ms_init returns.
   MS_TRY(cudaMalloc(&c->d_key, MS_KEY_BYTES));
+  if (key_dev) {  // a clone: device to device, the key never passes through host memory
+    MS_TRY(cudaMemcpyAsync(c->d_key, key_dev, MS_KEY_BYTES, cudaMemcpyDeviceToDevice, c->stream));
+    MS_TRY(cudaEventRecord(c->sync_ev, c->stream));
+    const int krc = wait_event(c, c->sync_ev, cfg.timeout_ms);
+    if (krc != MS_OK) {
+      release(c);
+      return krc;
+    }
+  }
   uint8_t *bounce = nullptr;
-  MS_TRY(cudaHostAlloc(&bounce, MS_KEY_BYTES, cudaHostAllocDefault));
-  if (key) {
+  if (!key_dev) MS_TRY(cudaHostAlloc(&bounce, MS_KEY_BYTES, cudaHostAllocDefault));
+  if (key_dev) {
+    // nothing to place
+  } else if (key) {
     std::memcpy(bounce, key, MS_KEY_BYTES);
   } else {
     size_t got = 0;
@@ -305,14 +320,16 @@ int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg_in) {
       got += (size_t)r;
     }
   }
-  e = cudaMemcpyAsync(c->d_key, bounce, MS_KEY_BYTES, cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(c->sync_ev, c->stream);
-  int rc = (e == cudaSuccess) ? wait_event(c, c->sync_ev, cfg.timeout_ms) : MS_ECUDA;
-  explicit_bzero(bounce, MS_KEY_BYTES);
-  cudaFreeHost(bounce);
-  if (rc != MS_OK) {
-    release(c);
-    return rc;
+  if (!key_dev) {
+    e = cudaMemcpyAsync(c->d_key, bounce, MS_KEY_BYTES, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->sync_ev, c->stream);
+    int rc = (e == cudaSuccess) ? wait_event(c, c->sync_ev, cfg.timeout_ms) : MS_ECUDA;
+    explicit_bzero(bounce, MS_KEY_BYTES);
+    cudaFreeHost(bounce);
+    if (rc != MS_OK) {
+      release(c);
+      return rc;
+    }
   }
 #undef MS_TRY
 
@@ -329,6 +346,33 @@ int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg_in) {
     return MS_EINVAL;
   }
   c->alive = true;
+  *out = c;
+  return MS_OK;
+}
+
+}  // namespace
+
+int ms_init(ms_ctx **out, const uint8_t *key, const ms_config *cfg) { return init_ctx(out, key, nullptr, cfg); }
+
+int ms_clone(ms_ctx *parent, uint32_t domain, ms_ctx **out) {
+  if (!out) return MS_EINVAL;
+  *out = nullptr;
+  if (!parent || !parent->alive) return MS_ENOTINIT;
+  ms_config cfg = parent->cfg;
+  cfg.domain = domain;
+  cfg.stream = nullptr;  // its own stream
+  cfg.use_stream = 0;
+  // the parent's shape, explicit or tuned, is taken over below
+  cfg.blocks_per_thread = cfg.threads_per_cta = cfg.dr_unroll = 0;
+  ms_ctx *c = nullptr;
+  const int rc = init_ctx(&c, nullptr, parent->d_key, &cfg);
+  if (rc != MS_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lk(parent->mu);
+    c->tune = parent->tune;
+    c->qtune = parent->qtune;
+    c->shape_explicit = parent->shape_explicit;
+  }
   *out = c;
   return MS_OK;
 }

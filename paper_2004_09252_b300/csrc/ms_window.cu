@@ -306,13 +306,19 @@ extern "C" int ms_window_run_ticketed(ms_ctx *ctx, void *host_base, uint64_t n_p
                                       const ms_window_client *clients, size_t n_clients, ms_window_stats *stats_out,
                                       uint64_t *final_window_out, uint32_t timeout_ms) {
   if (!ctx || !host_base || n_pages == 0) return MS_EINVAL;
-  const int rc = check_window_args(cfg, clients, n_clients, n_pages);
+  int rc = check_window_args(cfg, clients, n_clients, n_pages);
   if (rc != MS_OK) return rc;
-  for (size_t c = 0; c < n_clients; ++c)
-    if (clients[c].domain != ctx->cfg.domain) return MS_EINVAL;  // one context, one domain
   uint64_t dbase = 0;
   if (ms_host_device_address(host_base, &dbase) != MS_OK) return MS_EINVAL;
-  return run_clients(*cfg, clients, n_clients, stats_out, final_window_out, [&](const ms_window_client &) {
-    return TicketBackend{ctx, dbase, timeout_ms, ~0ull, {}};
-  });
+  // one clone per client: its PID as the domain, its own stream
+  std::vector<ms_ctx *> clones(n_clients, nullptr);
+  for (size_t c = 0; c < n_clients && rc == MS_OK; ++c) rc = ms_clone(ctx, clients[c].domain, &clones[c]);
+  if (rc == MS_OK) {
+    rc = run_clients(*cfg, clients, n_clients, stats_out, final_window_out, [&](const ms_window_client &cl) {
+      return TicketBackend{clones[(size_t)(&cl - clients)], dbase, timeout_ms, ~0ull, {}};
+    });
+  }
+  for (ms_ctx *k : clones)
+    if (k) ms_shutdown(k);
+  return rc;
 }

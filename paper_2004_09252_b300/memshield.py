@@ -213,6 +213,7 @@ def _load():
                               ctypes.POINTER(ms_window_stats), P, ctypes.c_uint32]),
         "ms_probe_int_pipes": (I, [I, ctypes.POINTER(ms_pipe_rate), S]),
         "ms_submit_host": (I, [P, I, P, S, ctypes.POINTER(U64)]),
+        "ms_clone": (I, [P, ctypes.c_uint32, ctypes.POINTER(P)]),
         "ms_poll": (I, [P, U64]),
         "ms_wait": (I, [P, U64, ctypes.c_uint32]),
         "ms_host_device_address": (I, [P, ctypes.POINTER(U64)]),
@@ -345,6 +346,15 @@ class Context:
         self.handle = h.value
         self.cfg = cfg
 
+    def clone(self, domain: int) -> "Context":
+        """ms_clone: the same key (device to device), another domain, its own stream."""
+        h = ctypes.c_void_p()
+        _check(_lib.ms_clone(self.handle, domain, ctypes.byref(h)), "ms_clone")
+        c = Context.__new__(Context)
+        c.handle = h.value
+        c.cfg = None
+        return c
+
     # -- one-launch forms
     def encrypt_pages(self, pages: np.ndarray) -> None:
         pages = np.ascontiguousarray(pages, dtype=PAGE_DTYPE)
@@ -413,9 +423,9 @@ class Context:
 
     def run_window_clients(self, host_base, n_pages: int, window_pages: int, evict_batch: int, clients,
                            timeout_ms: int = 60000):
-        """Sliding-window clients served by ticketed launches on this context, in
-        place on a pinned, mapped working set (every client's domain must be the
-        context's)."""
+        """Sliding-window clients served by ticketed launches, one clone of this
+        context per client (its domain, its stream), in place on a pinned, mapped
+        working set."""
         base = _ptr(host_base)
         return _run_window(lambda cfg, arr, n, st, fw: _lib.ms_window_run_ticketed(
             self.handle, base, n_pages, cfg, arr, n, st, fw, timeout_ms),

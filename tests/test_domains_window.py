@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import PAGE
+from helpers import PAGE, oracle_expected
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -143,29 +143,62 @@ def test_sliding_window_clients_on_resident_workers(ms, key1, window, batch):
 
 @pytest.mark.parametrize("window,batch", [(4, 1), (16, 9)])
 def test_sliding_window_clients_on_ticketed_launches(ms, key1, window, batch):
-    """The same clients served by one ticketed launch per fault and per eviction
-    on a context (domain 77, shared by every client): the same final state."""
+    """The same clients served by one ticketed launch per fault and per eviction,
+    each client on its own clone of the context (its PID, its stream): the same
+    final state."""
     per, n_clients = 128, 3
     n = per * n_clients
     plain = synth.page_bytes_fast(296, 0, n)
     h = torch.from_numpy(plain.copy()).pin_memory()
-    dom = 77
-    clients = [(dom, c * per, per, synth.window_trace(297 + c, per, 1500)) for c in range(n_clients)]
-    with ms.Context(key1, domain=dom) as ctx:
+    doms = [501, 502, 503]
+    clients = [(doms[c], c * per, per, synth.window_trace(297 + c, per, 1500)) for c in range(n_clients)]
+    with ms.Context(key1) as ctx:
         base = ms.host_device_address(h)
-        ids = np.arange(n, dtype=np.uint64)
-        ctx.wait(ctx.submit_host(ms.MS_ENCRYPT, ms.pages_array(base + PAGE * ids, ids)))   # all start encrypted
+        for c in range(n_clients):                             # all start encrypted under their PID
+            ids = np.arange(c * per, (c + 1) * per, dtype=np.uint64)
+            k = ctx.clone(doms[c])
+            k.wait(k.submit_host(ms.MS_ENCRYPT, ms.pages_array(base + PAGE * ids, ids)))
+            k.shutdown()
         stats, wins = ctx.run_window_clients(h, n, window, batch, clients)
-        with pytest.raises(ms.MemShieldError):                 # a client with another domain
-            ctx.run_window_clients(h, n, window, batch, [(dom + 1, 0, per, clients[0][3])])
     ws = h.numpy()
     for c in range(n_clients):
         st, win = stats[c], wins[c]
         assert st["accesses"] == 1500 and st["faults"] - st["evictions"] == len(win) <= window
         enc = np.array(sorted(set(range(c * per, (c + 1) * per)) - set(win)), dtype=np.uint64)
         want = plain[c * per * PAGE:(c + 1) * per * PAGE].copy()
-        oracle.crypt_pages(key1, want, enc - np.uint64(c * per), enc, domain=dom)
+        oracle.crypt_pages(key1, want, enc - np.uint64(c * per), enc, domain=doms[c])
         assert np.array_equal(ws[c * per * PAGE:(c + 1) * per * PAGE], want), f"client {c}"
+
+
+def test_clone_keeps_the_key_and_takes_its_domain(ms, key1):
+    """A clone encrypts with the parent's key under its own domain, on its own
+    stream; the parent is unchanged; a clone of a clone works too."""
+    n = 40
+    plain = synth.page_bytes(298, 0, n)
+    ids = np.arange(n, dtype=np.uint64)
+    with ms.Context(key1, domain=7) as ctx:
+        ctx.set_shape(2, 256, 10, 1)
+        k = ctx.clone(9)
+        k2 = k.clone(11)
+        assert k.get_shape() == ctx.get_shape()
+        for c, dom in ((ctx, 7), (k, 9), (k2, 11)):
+            d = torch.from_numpy(plain).cuda()
+            torch.cuda.synchronize()
+            c.encrypt_pages(ms.pages_array(d.data_ptr() + PAGE * ids, ids))
+            c.sync_checked()
+            assert np.array_equal(d.cpu().numpy(), oracle_expected(key1, plain, ids, ids, domain=dom))
+        k2.shutdown()
+        k.shutdown()
+    with ms.Context(None) as rnd:                              # a random key: the clone matches it
+        k = rnd.clone(0)
+        a, b = torch.from_numpy(plain).cuda(), torch.from_numpy(plain).cuda()
+        torch.cuda.synchronize()
+        rnd.encrypt_pages(ms.pages_array(a.data_ptr() + PAGE * ids, ids))
+        k.encrypt_pages(ms.pages_array(b.data_ptr() + PAGE * ids, ids))
+        rnd.sync_checked()
+        k.sync_checked()
+        assert torch.equal(a, b) and not np.array_equal(a.cpu().numpy(), plain)
+        k.shutdown()
 
 
 def test_window_rejects_bad_configs(ms, key1):
