@@ -193,8 +193,10 @@ int ms_sync_for(ms_ctx *ctx, uint32_t timeout_ms);
 /*
  * Finish outstanding work (bounded), overwrite the device key with zeros and
  * free every resource.  ctx must not be used afterwards.  NULL is a no-op.
- * MS_EBUSY (and nothing is freed) while a batch, server or resident worker
- * set created on the context has not been destroyed.
+ * MS_EBUSY (and nothing is freed) while a batch, feed, server or resident
+ * worker set created on the context has not been destroyed.  MS_ETIMEDOUT
+ * (and nothing is touched: the context stays usable, call again) when the
+ * queued work does not finish within timeout_ms.
  */
 int ms_shutdown(ms_ctx *ctx);
 

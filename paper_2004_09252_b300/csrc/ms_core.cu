@@ -294,7 +294,7 @@ int init_ctx(ms_ctx **out, const uint8_t *key, const uint4 *key_dev, const ms_co
   if (key_dev) {  // a clone: device to device, the key never passes through host memory
     MS_TRY(cudaMemcpyAsync(c->d_key, key_dev, MS_KEY_BYTES, cudaMemcpyDeviceToDevice, c->stream));
     MS_TRY(cudaEventRecord(c->sync_ev, c->stream));
-    const int krc = wait_event(c, c->sync_ev, cfg.timeout_ms);
+    const int krc = wait_event(c, c->sync_ev, std::max<uint32_t>(cfg.timeout_ms, 1000));
     if (krc != MS_OK) {
       release(c);
       return krc;
@@ -323,7 +323,7 @@ int init_ctx(ms_ctx **out, const uint8_t *key, const uint4 *key_dev, const ms_co
   if (!key_dev) {
     e = cudaMemcpyAsync(c->d_key, bounce, MS_KEY_BYTES, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaEventRecord(c->sync_ev, c->stream);
-    int rc = (e == cudaSuccess) ? wait_event(c, c->sync_ev, cfg.timeout_ms) : MS_ECUDA;
+    int rc = (e == cudaSuccess) ? wait_event(c, c->sync_ev, std::max<uint32_t>(cfg.timeout_ms, 1000)) : MS_ECUDA;
     explicit_bzero(bounce, MS_KEY_BYTES);
     cudaFreeHost(bounce);
     if (rc != MS_OK) {
@@ -531,24 +531,29 @@ int ms_sync_for(ms_ctx *c, uint32_t timeout_ms) {
 int ms_shutdown(ms_ctx *c) {
   if (!c) return MS_OK;
   if (c->children.load() > 0) return MS_EBUSY;  // a batch, server or resident set still uses it
-  int rc = MS_OK;
-  {
-    DeviceGuard g(c->device);
-    if (c->alive) {
-      // finish queued work (bounded), then overwrite the key on the device
-      cudaEventRecord(c->sync_ev, c->stream);
-      rc = wait_event(c, c->sync_ev, c->cfg.timeout_ms);
-      if (c->d_key) cudaMemsetAsync(c->d_key, 0, MS_KEY_BYTES, c->stream);
-      cudaEventRecord(c->sync_ev, c->stream);
-      int rc2 = wait_event(c, c->sync_ev, c->cfg.timeout_ms);
-      if (rc == MS_OK) rc = rc2;
-      for (int i = 0; i < kMaxHostStreams; ++i)
-        if (c->hs[i]) cudaStreamSynchronize(c->hs[i]);
-    }
+  DeviceGuard g(c->device);
+  if (c->alive) {
+    std::lock_guard<std::mutex> lk(c->mu);
+    // Finish queued work (bounded).  If it does not finish, nothing is
+    // touched: kernels still queued read the key and the buffers, so the
+    // context stays as it is and the call can be repeated.
+    cudaError_t e = cudaEventRecord(c->sync_ev, c->stream);
+    int rc = e == cudaSuccess ? wait_event(c, c->sync_ev, c->cfg.timeout_ms) : cuda_fail(c, e);
+    for (int i = 0; i < kMaxHostStreams && rc == MS_OK; ++i)
+      if (c->hs[i]) {
+        e = cudaEventRecord(c->hs_ev[i], c->hs[i]);
+        rc = e == cudaSuccess ? wait_event(c, c->hs_ev[i], c->cfg.timeout_ms) : cuda_fail(c, e);
+      }
+    if (rc != MS_OK) return rc;
+    // then overwrite the key on the device
+    if (c->d_key) cudaMemsetAsync(c->d_key, 0, MS_KEY_BYTES, c->stream);
+    e = cudaEventRecord(c->sync_ev, c->stream);
+    rc = e == cudaSuccess ? wait_event(c, c->sync_ev, c->cfg.timeout_ms) : cuda_fail(c, e);
+    if (rc != MS_OK) return rc;
     c->alive = false;
-    release(c);
   }
-  return rc;
+  release(c);
+  return MS_OK;
 }
 
 int ms_get_shape(const ms_ctx *c, ms_shape *out) {

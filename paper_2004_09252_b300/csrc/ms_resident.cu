@@ -398,23 +398,22 @@ int ms_resident_get_stats(const ms_resident *r, ms_resident_stats *out) {
 int ms_resident_destroy(ms_resident *r) {
   if (!r) return MS_OK;
   DeviceGuard g(r->ctx->device);
-  int rc = MS_OK;
   for (Worker *w : r->w) __atomic_store_n(&w->h_sh->stop, 1u, __ATOMIC_RELEASE);
+  // Every worker must be known to have left before its rings are freed; if
+  // that cannot be established, the memory stays allocated.
   for (Worker *w : r->w) {
     cudaEvent_t ev;
-    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
-      rc = MS_ECUDA;
-      continue;
-    }
-    cudaEventRecord(ev, w->stream);
-    const int r2 = wait_event(r->ctx, ev, r->ctx->cfg.timeout_ms);
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(r->ctx, e);
+    e = cudaEventRecord(ev, w->stream);
+    const int r2 = e == cudaSuccess ? wait_event(r->ctx, ev, r->ctx->cfg.timeout_ms) : cuda_fail(r->ctx, e);
     cudaEventDestroy(ev);
-    if (r2 != MS_OK) return r2;  // a worker still runs: keep its memory allocated
+    if (r2 != MS_OK) return r2;
   }
   ms_ctx *c = r->ctx;
   free_resident(r);
   c->children.fetch_sub(1);
-  return rc;
+  return MS_OK;
 }
 
 }  // extern "C"

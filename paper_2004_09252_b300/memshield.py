@@ -457,10 +457,11 @@ class Context:
         return _lib.ms_last_cuda_error(self.handle)
 
     def shutdown(self) -> int:
-        """ms_shutdown; the handle stays valid when it returns MS_EBUSY (children alive)."""
+        """ms_shutdown; the handle stays valid when it returns MS_EBUSY (children
+        alive) or MS_ETIMEDOUT (queued work still running)."""
         if self.handle:
             rc = _lib.ms_shutdown(self.handle)
-            if rc != MS_EBUSY:
+            if rc not in (MS_EBUSY, MS_ETIMEDOUT):
                 self.handle = None
             return rc
         return MS_OK

@@ -87,3 +87,23 @@ def test_ticket_wait_is_not_held_up_by_a_sync(ms, key1):
         th.join()
         assert done["sync_rc"] == ms.MS_OK
         assert t_ticket < done["sync_t"]
+
+
+def test_shutdown_with_work_still_queued_times_out_and_keeps_the_context(ms, key1):
+    """A shutdown whose bounded wait runs out touches nothing: the queued work
+    finishes with the key intact, and a later shutdown succeeds."""
+    n = 262144
+    plain = synth.page_bytes_fast(84, 0, 64)
+    d = torch.zeros(n * PAGE, dtype=torch.uint8, device="cuda")
+    d[:64 * PAGE] = torch.from_numpy(plain).cuda()
+    torch.cuda.synchronize()
+    ctx = ms.Context(key1, timeout_ms=1)
+    for _ in range(41):                                   # ~25 ms of queued work, odd count
+        ctx.crypt_range(ms.MS_ENCRYPT, d, 0, n)
+    assert ctx.shutdown() == ms.MS_ETIMEDOUT               # 1 ms is not enough
+    assert ctx.handle is not None
+    while ctx.sync_for(10) == ms.MS_ETIMEDOUT:             # the context still works
+        pass
+    assert ctx.shutdown() == ms.MS_OK
+    ids = np.arange(64, dtype=np.uint64)
+    assert np.array_equal(d[:64 * PAGE].cpu().numpy(), oracle_expected(key1, plain, ids, ids))
