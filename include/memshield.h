@@ -331,7 +331,8 @@ int ms_batch_add_requests(ms_batch *batch, size_t n_requests, const int *ops, co
 /* Copy the queued requests to the device and launch K2; asynchronous (ms_sync). */
 int ms_batch_submit(ms_batch *batch);
 int ms_batch_get_stats(const ms_batch *batch, ms_batch_stats *out);
-/* Waits (bounded) for the batch's work, then frees it.  NULL is a no-op. */
+/* Waits (bounded) for the batch's work, then frees it.  NULL is a no-op.
+ * MS_ETIMEDOUT (nothing freed; call again) if the work does not finish. */
 int ms_batch_destroy(ms_batch *batch);
 
 /*

@@ -46,17 +46,22 @@ using namespace ms;
 
 namespace {
 
-int free_batch(ms_batch *b) {
-  int rc = MS_OK;
-  for (QBuf &q : b->buf) {
-    // An event never recorded counts as complete, so both waits are safe on
-    // buffers that were never submitted; a copy enqueued by a submit that
-    // failed later is waited for too.
+// Bounded wait for everything the batch issued.  An event never recorded
+// counts as complete, so buffers never submitted need no care; a copy
+// enqueued by a submit that failed later is waited for too.
+int wait_batch(ms_batch *b) {
+  for (QBuf &q : b->buf)
     for (cudaEvent_t ev : {q.copied, q.done})
       if (ev) {
-        int r = wait_event(b->ctx, ev, b->ctx->cfg.timeout_ms);
-        if (r != MS_OK && rc == MS_OK) rc = r;
+        const int r = wait_event(b->ctx, ev, b->ctx->cfg.timeout_ms);
+        if (r != MS_OK) return r;
       }
+  return MS_OK;
+}
+
+// Frees a batch whose work has finished (or was never issued).
+void free_batch(ms_batch *b) {
+  for (QBuf &q : b->buf) {
     if (q.exec) cudaGraphExecDestroy(q.exec);
     if (q.done) cudaEventDestroy(q.done);
     if (q.copied) cudaEventDestroy(q.copied);
@@ -65,7 +70,6 @@ int free_batch(ms_batch *b) {
   }
   if (b->copy_stream) cudaStreamDestroy(b->copy_stream);
   delete b;
-  return rc;
 }
 
 // The K2 launch parameters of this batch (config overrides, else the context's tuning).
@@ -335,9 +339,11 @@ int ms_batch_destroy(ms_batch *b) {
   if (!b) return MS_OK;
   ms_ctx *c = b->ctx;
   DeviceGuard g(c->device);
-  const int rc = free_batch(b);
+  const int rc = wait_batch(b);
+  if (rc != MS_OK) return rc;  // still in use on the GPU: keep it allocated
+  free_batch(b);
   c->children.fetch_sub(1);
-  return rc;
+  return MS_OK;
 }
 
 }  // extern "C"

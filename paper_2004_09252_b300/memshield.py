@@ -525,7 +525,8 @@ class Feed:
     def destroy(self) -> int:
         if self.handle:
             rc = _lib.ms_feed_destroy(self.handle)
-            self.handle = None
+            if rc != MS_ETIMEDOUT:  # still in use on the GPU: the handle stays valid, call again
+                self.handle = None
             return rc
         return MS_OK
 
@@ -596,7 +597,8 @@ class Batch:
     def destroy(self) -> int:
         if self.handle:
             rc = _lib.ms_batch_destroy(self.handle)
-            self.handle = None
+            if rc != MS_ETIMEDOUT:  # still in use on the GPU: the handle stays valid, call again
+                self.handle = None
             return rc
         return MS_OK
 
@@ -685,7 +687,8 @@ class Server:
     def destroy(self) -> int:
         if self.handle:
             rc = _lib.ms_server_destroy(self.handle)
-            self.handle = None
+            if rc != MS_ETIMEDOUT:  # still in use on the GPU: the handle stays valid, call again
+                self.handle = None
             return rc
         return MS_OK
 
@@ -781,7 +784,8 @@ class Resident:
     def destroy(self) -> int:
         if self.handle:
             rc = _lib.ms_resident_destroy(self.handle)
-            self.handle = None
+            if rc != MS_ETIMEDOUT:  # still in use on the GPU: the handle stays valid, call again
+                self.handle = None
             return rc
         return MS_OK
 
