@@ -130,3 +130,24 @@ def test_a_starved_feed_reports_and_the_context_recovers(ms, key1):
         ctx.encrypt_pages(ms.pages_array(d2.data_ptr() + PAGE * ids, ids))
         ctx.sync_checked()
         assert np.array_equal(d2.cpu().numpy(), oracle_expected(key1, plain, ids, ids))
+
+
+@pytest.mark.parametrize("rounds,bpt", [(12, 4), (8, 2), (20, 1), (20, 2)])
+def test_fed_queue_reduced_rounds_and_shapes(ms, key1, rounds, bpt):
+    """The fed kernel's other instances: ChaCha12 / ChaCha8 and 1 or 2 blocks
+    per thread (taken from the context's shape)."""
+    n_slots = 5000
+    slots, offsets, ops = request_table(185, n_slots, 150, 30)
+    plain = synth.page_bytes_fast(186, 0, n_slots)
+    d = torch.from_numpy(plain).cuda()
+    torch.cuda.synchronize()
+    table = ms.pages_array(d.data_ptr() + PAGE * slots, slots)
+    with ms.Context(key1, rounds=rounds) as ctx:
+        if bpt != 4:
+            ctx.set_shape(bpt, 128, rounds // 2, 1, 1 if bpt >= 2 else 0)
+        with ctx.feed(capacity=len(slots), chunk=1024) as f:
+            f.open()
+            assert f.add_requests(ops, offsets, table) == len(ops)
+            f.close()
+            ctx.sync_checked()
+    assert np.array_equal(d.cpu().numpy(), oracle_expected(key1, plain, slots, slots, rounds=rounds))
