@@ -659,7 +659,9 @@ typedef struct ms_feed_stats {
 } ms_feed_stats;
 
 void ms_feed_config_default(ms_feed_config *cfg);
-/* Allocates 2 x 16 B x capacity (pinned + device); launches nothing. */
+/* Allocates 2 x 16 B x capacity (pinned + device) and loads the kernel, in
+ * the context's current shape, so that a run pays for neither; launches
+ * nothing. */
 int ms_feed_create(ms_ctx *ctx, const ms_feed_config *cfg, ms_feed **out);
 /* Launch the kernel over an empty queue, after the previous run (if any) has
  * drained (bounded wait).  MS_EBUSY if already open. */

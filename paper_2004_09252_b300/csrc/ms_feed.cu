@@ -29,6 +29,7 @@ namespace {
 constexpr uint32_t kMinChunk = 1024;  // entries per publication, at least
 constexpr int kHeadWord = 32;         // the claimed head apart from the polled words
 constexpr int kCtlWords = 64;
+constexpr int kFeedThreads = 128;     // threads per CTA
 
 struct FeedArgs {
   const ms_page *items;   // device queue
@@ -191,6 +192,8 @@ struct ms_feed {
   bool closed = false;
   cudaStream_t cs = nullptr;
   cudaEvent_t started = nullptr, done = nullptr;
+  const FeedEntry *kernel = nullptr;  // the instance chosen (and loaded) at creation
+  int grid = 0;                       // persistent CTAs: all of it that fit
   std::mutex mu;
   ms_feed_stats stats{};
 };
@@ -276,6 +279,17 @@ int ms_feed_create(ms_ctx *c, const ms_feed_config *cfg_in, ms_feed **out) {
     return alloc_fail(c, e);
   }
   *f->h_one = 1;
+  // Load the kernel and size its grid now (the occupancy query loads the
+  // module), so that neither falls into a run.
+  const FeedEntry *k = feed_kernel(c);
+  f->kernel = k;
+  int fit = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k->fn, kFeedThreads, 0);
+  if (e != cudaSuccess) {
+    free_feed(f);
+    return cuda_fail(c, e);
+  }
+  f->grid = (fit < 1 ? 1 : fit) * c->sm_count;
   c->children.fetch_add(1);
   *out = f;
   return MS_OK;
@@ -299,7 +313,7 @@ int ms_feed_open(ms_feed *f) {
     cudaEventDestroy(ev);
   }
   if (rc != MS_OK) return rc;
-  const FeedEntry *k = feed_kernel(c);
+  const FeedEntry *k = f->kernel;
   std::lock_guard<std::mutex> lk2(c->mu);
   // control words zeroed on the context stream, then the kernel; the copy
   // stream starts after the zeroing, so no publication is overwritten
@@ -318,19 +332,15 @@ int ms_feed_open(ms_feed *f) {
   a.status = c->d_status;
   a.mc.m12 = 1u << 12;
   a.mc.m7 = 1u << 7;
-  const int tpc = 128;
-  int fit = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k->fn, tpc, 0);
-  if (fit < 1) fit = 1;
   if (e == cudaSuccess) e = injected(MS_FAULT_LAUNCH);
-  if (e == cudaSuccess) e = k->launch(a, fit * c->sm_count, tpc, c->stream);
+  if (e == cudaSuccess) e = k->launch(a, f->grid, kFeedThreads, c->stream);
   if (e == cudaSuccess) e = cudaEventRecord(f->done, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e);  // a kernel that did start leaves by its bounded wait
   c->status_dirty = true;  // the kernel may report a starved wait or a bad entry
   f->filled = f->published = 0;
   f->n_pub = 0;
   f->closed = false;
-  f->stats.grid = (uint64_t)(fit * c->sm_count);
+  f->stats.grid = (uint64_t)f->grid;
   f->stats.runs += 1;
   return MS_OK;
 }
