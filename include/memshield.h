@@ -34,6 +34,22 @@
  * Errors: every int-returning call returns MS_OK (0) or a negative MS_E* code;
  * ms_strerror() names it.  n = 0 is a successful no-op.  Calls on one context
  * may come from several host threads; submissions are serialised internally.
+ *
+ * Contents:
+ *   contexts            ms_init, ms_clone, ms_sync, ms_shutdown
+ *   one launch          ms_encrypt_pages / ms_decrypt_pages (host list),
+ *                       *_dev (device list), ms_crypt_pages_dom*, ms_crypt_range
+ *   tickets             ms_submit_host, ms_poll, ms_wait
+ *   host streaming      ms_crypt_host
+ *   shape and tuning    ms_get_shape / ms_set_shape, ms_autotune, ms_tune_save/load
+ *   batched             ms_batch_* (persistent kernel, device queue, CUDA graphs)
+ *   served              ms_server_* (continuous batching over a host working set)
+ *   sliding window      ms_window_run, ms_window_run_resident, ms_window_run_ticketed
+ *   resident workers    ms_resident_* (always-running kernels fed through mapped rings)
+ *   allocation-free     ms_crypt_pages_noalloc
+ *   fed                 ms_feed_* (one persistent kernel fed while it runs)
+ *   measurement         ms_probe_int_pipes
+ *   testing             ms_debug_inject_fault (host-side failure injection)
  */
 #ifndef MEMSHIELD_H
 #define MEMSHIELD_H
