@@ -24,6 +24,7 @@
 #include <atomic>
 #include <chrono>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -438,52 +439,74 @@ extern "C" int ms_resident_replay(ms_resident *r, void *host_base, uint64_t n_pa
     }
   }
   for (size_t q = 0; q < n; ++q) {
-    latency_s[q] = -1.0;
+    if (offsets[q + 1] <= offsets[q]) return MS_EINVAL;  // every request has at least one page
     for (uint64_t k = offsets[q]; k < offsets[q + 1]; ++k)
       if (page_index[k] >= n_pages) return MS_EINVAL;
+    latency_s[q] = -1.0;
   }
-  std::vector<uint64_t> tickets(offsets[n]);
+  if (n > UINT32_MAX) return MS_ERANGE;
+  const uint32_t W = r->cfg.workers;
+  const uint64_t total = offsets[n];
+  // Completion is followed per worker, in ring order (a worker serves its
+  // requests in order): each pass advances every worker's frontier over the
+  // pages it has finished, which is O(completions), and a request is stamped
+  // when its last page finishes.  wmap[w][i] is the request of the i-th page
+  // this replay gave worker w; it is written before that page is published.
+  std::vector<uint64_t> tickets(total);
   std::vector<uint64_t> sched(n);
-  std::vector<uint8_t> done_flag(n, 0);
+  std::vector<uint32_t> remaining(n);
+  for (size_t q = 0; q < n; ++q) remaining[q] = (uint32_t)(offsets[q + 1] - offsets[q]);
   std::vector<uint64_t> last_ticket(n_pages, ~0ull);
-  std::atomic<size_t> submitted{0};
+  std::vector<std::vector<uint32_t>> wmap(W, std::vector<uint32_t>(total / W + 2));
+  std::vector<uint64_t> base_li(W);
+  for (uint32_t w = 0; w < W; ++w) {
+    std::lock_guard<std::mutex> lk(r->w[w]->mu);
+    base_li[w] = r->w[w]->tail;
+  }
+  std::unique_ptr<std::atomic<uint64_t>[]> published(new std::atomic<uint64_t>[W]);
+  for (uint32_t w = 0; w < W; ++w) published[w].store(0);
   std::atomic<int> err{0};
   auto now_ns = [] {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(clk::now().time_since_epoch()).count();
   };
   const uint64_t t0 = now_ns() + 1000000ull;
-  // completer: timestamps requests as all their pages finish
   std::thread comp([&] {
-    size_t first_open = 0;
+    std::vector<uint64_t> frontier(W, 0);
+    size_t completed = 0;
     const uint64_t deadline_pad = (uint64_t)timeout_ms * 1000000ull;
     uint64_t last_progress = now_ns();
-    while (first_open < n && !err.load()) {
-      const size_t hi = submitted.load(std::memory_order_acquire);
+    while (completed < n && !err.load()) {
       bool progress = false;
-      for (size_t q = first_open; q < hi && q < first_open + 4096; ++q) {
-        if (done_flag[q]) continue;
-        bool all = true;
-        for (uint64_t k = offsets[q]; k < offsets[q + 1] && all; ++k) all = ms_resident_poll(r, tickets[k]) == 1;
-        if (all) {
-          const uint64_t t = now_ns();
-          latency_s[q] = (double)(int64_t)(t - sched[q]) * 1e-9;
-          done_flag[q] = 1;
+      for (uint32_t w = 0; w < W; ++w) {
+        const uint64_t hi = published[w].load(std::memory_order_acquire);
+        while (frontier[w] < hi) {
+          const uint64_t ticket = (base_li[w] + frontier[w]) * W + w;
+          if (ms_resident_poll(r, ticket) != 1) break;
+          const uint32_t q = wmap[w][frontier[w]];
+          if (--remaining[q] == 0) {
+            latency_s[q] = (double)(int64_t)(now_ns() - sched[q]) * 1e-9;
+            ++completed;
+          }
+          ++frontier[w];
           progress = true;
         }
       }
-      while (first_open < hi && done_flag[first_open]) ++first_open;
       const uint64_t t = now_ns();
-      if (progress) last_progress = t;
-      if (first_open < hi && t - last_progress > deadline_pad) {
-        // the oldest request is stuck: let ms_resident_wait relaunch a worker that left
-        for (uint64_t k = offsets[first_open]; k < offsets[first_open + 1]; ++k)
-          if (ms_resident_wait(r, tickets[k], timeout_ms) != MS_OK) {
+      if (progress) {
+        last_progress = t;
+        continue;
+      }
+      if (t - last_progress > deadline_pad) {
+        // nothing finished for timeout_ms: let ms_resident_wait relaunch a worker that left
+        for (uint32_t w = 0; w < W; ++w)
+          if (frontier[w] < published[w].load(std::memory_order_acquire) &&
+              ms_resident_wait(r, (base_li[w] + frontier[w]) * W + w, timeout_ms) != MS_OK) {
             err.store(MS_ETIMEDOUT);
             return;
           }
         last_progress = now_ns();
       }
-      if (!progress) nap_ns(2000);
+      nap_ns(2000);
     }
   });
   int rc = MS_OK;
@@ -515,9 +538,18 @@ extern "C" int ms_resident_replay(ms_resident *r, void *host_base, uint64_t n_pa
         }
         nap_ns(2000);
       }
-      if (rc == MS_OK) last_ticket[pg] = tickets[k];
+      if (rc == MS_OK) {
+        last_ticket[pg] = tickets[k];
+        const uint32_t w = (uint32_t)(tickets[k] % W);
+        const uint64_t idx = tickets[k] / W - base_li[w];
+        if (idx >= wmap[w].size() || idx != published[w].load(std::memory_order_relaxed)) {
+          rc = MS_EBUSY;  // another thread submitted to these workers during the replay
+          break;
+        }
+        wmap[w][idx] = (uint32_t)q;
+        published[w].store(idx + 1, std::memory_order_release);
+      }
     }
-    if (rc == MS_OK) submitted.store(q + 1, std::memory_order_release);
   }
   if (rc != MS_OK) err.store(rc);
   comp.join();
