@@ -209,6 +209,7 @@ struct Worker {
   WorkerShared *h_sh = nullptr, *d_sh = nullptr;
   cudaStream_t stream = nullptr;
   uint64_t tail = 0;  // next local index to fill
+  uint64_t done_hint = 0;  // every local index below this is known finished (under mu)
   std::mutex mu;
   uint64_t host_launches = 0;
 };
@@ -252,6 +253,7 @@ int ensure_running(ms_resident *r, int wi) {
   }
   if (st == kRunning) return MS_OK;
   // EXITED (or never started): launch again; stream order puts it after the old launch
+  DeviceGuard g(r->ctx->device);  // only a launch needs the device current
   ResidentArgs a{};
   a.ring = w.d_ring;
   a.done = w.d_done;
@@ -338,16 +340,28 @@ int ms_resident_submit(ms_resident *r, const ms_page_dom *page, uint64_t *ticket
   Worker &w = *r->w[wi];
   std::lock_guard<std::mutex> lk(w.mu);
   const uint64_t li = w.tail;
-  const uint32_t slot = (uint32_t)(li & (r->cfg.ring_entries - 1));
-  if (li >= r->cfg.ring_entries && load_acq(&w.h_done[slot]) < li - r->cfg.ring_entries + 1)
-    return MS_EBUSY;  // the slot's previous request is still being served
+  const uint32_t R = r->cfg.ring_entries;
+  const uint32_t slot = (uint32_t)(li & (R - 1));
+  if (li >= R && w.done_hint < li - R + 1) {
+    // The slot's previous request (li - R) must have finished.  A worker
+    // finishes in order, so one done word proves every earlier index done:
+    // look halfway back first, which keeps these reads of GPU-written words
+    // to about two per R / 2 submissions.
+    const uint64_t probe = li - R / 2;
+    if (load_acq(&w.h_done[probe & (R - 1)]) >= probe + 1) {
+      w.done_hint = probe + 1;
+    } else if (load_acq(&w.h_done[slot]) >= li - R + 1) {
+      w.done_hint = li - R + 1;
+    } else {
+      return MS_EBUSY;  // the slot's previous request is still being served
+    }
+  }
   RingEntry &e = w.h_ring[slot];
   e.addr = page->addr;
   e.page_id = page->page_id;
   e.domain = page->domain;
   __atomic_store_n(&e.seq, li + 1, __ATOMIC_RELEASE);
-  w.tail = li + 1;
-  DeviceGuard g(r->ctx->device);
+  __atomic_store_n(&w.tail, li + 1, __ATOMIC_RELAXED);  // read without the lock by ms_resident_poll
   const int rc = ensure_running(r, wi);
   if (rc != MS_OK) return rc;
   *ticket = li * W + (uint64_t)wi;
@@ -376,7 +390,6 @@ int ms_resident_wait(ms_resident *r, uint64_t ticket, uint32_t timeout_ms) {
     // a worker that left with this request queued (max_run_ms) is launched again
     if ((it & 63) == 63 && load_acq32(&w.h_sh->state) == kExited) {
       std::lock_guard<std::mutex> lk(w.mu);
-      DeviceGuard g(r->ctx->device);
       const int rc = ensure_running(r, wi);
       if (rc != MS_OK) return rc;
     }
@@ -469,6 +482,13 @@ extern "C" int ms_resident_replay(ms_resident *r, void *host_base, uint64_t n_pa
   auto now_ns = [] {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(clk::now().time_since_epoch()).count();
   };
+  // Start every worker before the clock does, so that no launch (or module
+  // load) falls on the first requests.
+  for (uint32_t w = 0; w < W; ++w) {
+    std::lock_guard<std::mutex> lk(r->w[w]->mu);
+    const int rc0 = ensure_running(r, (int)w);
+    if (rc0 != MS_OK) return rc0;
+  }
   const uint64_t t0 = now_ns() + 1000000ull;
   std::thread comp([&] {
     std::vector<uint64_t> frontier(W, 0);
