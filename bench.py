@@ -704,6 +704,45 @@ SERVE_WORKLOAD = ("serving: {n} pages ({gib:.0f} GiB) pinned host working set (s
                   "1-page decrypts / 20 % U{{8..64}}-page encrypts, 256 MiB staging budget, {sec:g} s per rate")
 
 
+def resident_multi(args, ms, ctx, ws, n, rate, seconds):
+    """The resident form fed by several client threads at once: thread t owns
+    pages [t*n/T, (t+1)*n/T) of the working set, its own resident worker set
+    (args.resident_workers each) and its own serving workload (seed 5 + t) at
+    rate / T.  Returns (all latencies, the longest makespan, pages)."""
+    import threading
+
+    import numpy as np
+
+    import synth
+    T = args.resident_submitters
+    part = n // T
+    loads = []
+    for t in range(T):
+        n_req = max(2000, int(rate / T / 8.0 * seconds))
+        arr, _, offs, pages = synth.serving_workload(5 + t, n_req, rate / T, part)
+        loads.append((arr, offs, pages.astype(np.uint64) + np.uint64(t * part)))
+    res = [ms.Resident(ctx, workers=args.resident_workers) for _ in range(T)]
+    out, errors = [None] * T, []
+
+    def client(t):
+        try:
+            arr, offs, pages = loads[t]
+            out[t] = res[t].replay(ws, n, arr, offs, pages, timeout_ms=60000)
+        except Exception as e:  # surfaced below
+            errors.append(e)
+    threads = [threading.Thread(target=client, args=(t,)) for t in range(T)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    for r in res:
+        r.destroy()
+    if errors:
+        raise errors[0]
+    lat = np.concatenate([out[t][0] for t in range(T)])
+    return lat, max(out[t][1] for t in range(T)), sum(int(loads[t][1][-1]) for t in range(T))
+
+
 def serve_rows(args, rates, modes, seconds):
     """Replay the serving workload at each rate in each mode; one row per (rate, mode)."""
     import numpy as np
@@ -729,7 +768,11 @@ def serve_rows(args, rates, modes, seconds):
         for name in modes:
             reps = []
             for _ in range(max(1, args.serve_reps)):
-                if name == "resident":
+                if name == "resident" and args.resident_submitters > 1:
+                    lat, makespan, total_mt = resident_multi(args, ms, ctx, ws, n, rate, seconds)
+                    st = {"waves": total_mt, "max_wave_requests": 1, "conflict_waits": 0, "budget_waits": 0,
+                          "gather_ns": 0, "scatter_ns": 0}
+                elif name == "resident":
                     with ms.Resident(ctx, workers=args.resident_workers) as res:
                         lat, makespan = res.replay(ws, n, arrival, offsets, pages, timeout_ms=60000)
                         rst = res.stats()
@@ -742,7 +785,7 @@ def serve_rows(args, rates, modes, seconds):
                                    zero_copy_max_pages=args.zero_copy_max_pages) as srv:
                         lat, makespan = srv.replay(arrival, ops, offsets, pages, timeout_ms=600000)
                         st = srv.stats()
-                total = int(offsets[-1])
+                total = st["waves"] if (name == "resident" and args.resident_submitters > 1) else int(offsets[-1])
                 us = lat * 1e6
                 reps.append({"sustained_pages_per_s": total / makespan, "p50_us": float(np.percentile(us, 50)),
                              "p99_us": float(np.percentile(us, 99)), "p999_us": float(np.percentile(us, 99.9)),
@@ -926,6 +969,8 @@ def main():
     ap.add_argument("--copy-threads", type=int, default=8)
     ap.add_argument("--serve-reps", type=int, default=1, help="repetitions per serving configuration (medians reported)")
     ap.add_argument("--resident-workers", type=int, default=8)
+    ap.add_argument("--resident-submitters", type=int, default=1,
+                    help="serving, resident mode: client threads, each with its own worker set and page range")
     ap.add_argument("--batching-scale", type=float, default=1.0, help="fraction of the batching workload (profiling)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--window-client-pages", type=int, default=16384)
