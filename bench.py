@@ -785,11 +785,18 @@ def serve_rows(args, rates, modes, seconds):
                                    zero_copy_max_pages=args.zero_copy_max_pages) as srv:
                         lat, makespan = srv.replay(arrival, ops, offsets, pages, timeout_ms=600000)
                         st = srv.stats()
-                total = st["waves"] if (name == "resident" and args.resident_submitters > 1) else int(offsets[-1])
+                multi = name == "resident" and args.resident_submitters > 1
+                total = st["waves"] if multi else int(offsets[-1])
                 us = lat * 1e6
+                # p99 of the requests scheduled in each second of the run (single-submitter runs)
+                by_sec = []
+                if not multi:
+                    sec = np.floor(arrival).astype(np.int64)
+                    by_sec = [round(float(np.percentile(us[sec == k], 99)), 1) for k in range(int(sec.max()) + 1)
+                              if (sec == k).any()]
                 reps.append({"sustained_pages_per_s": total / makespan, "p50_us": float(np.percentile(us, 50)),
                              "p99_us": float(np.percentile(us, 99)), "p999_us": float(np.percentile(us, 99.9)),
-                             "st": st})
+                             "by_sec": by_sec, "st": st})
             # medians over the repetitions (single-run tails are noisy on a shared host)
             med = {k: float(np.median([r[k] for r in reps])) for k in ("sustained_pages_per_s", "p50_us", "p99_us",
                                                                       "p999_us")}
@@ -799,6 +806,7 @@ def serve_rows(args, rates, modes, seconds):
                          "p50_us": round(med["p50_us"], 1), "p99_us": round(med["p99_us"], 1),
                          "p999_us": round(med["p999_us"], 1), "reps": len(reps),
                          "p99_us_each": [round(r["p99_us"], 1) for r in reps],
+                         "p99_us_by_second": [r["by_sec"] for r in reps],
                          "waves": st["waves"], "max_wave_requests": st["max_wave_requests"],
                          "conflict_waits": st["conflict_waits"], "budget_waits": st["budget_waits"],
                          "gather_s": round(st["gather_ns"] * 1e-9, 3), "scatter_s": round(st["scatter_ns"] * 1e-9, 3)})
