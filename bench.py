@@ -777,7 +777,7 @@ def serve_rows(args, rates, modes, seconds):
                         lat, makespan = res.replay(ws, n, arrival, offsets, pages, timeout_ms=60000)
                         rst = res.stats()
                     st = {"waves": rst["requests"], "max_wave_requests": 1, "conflict_waits": 0, "budget_waits": 0,
-                          "gather_ns": 0, "scatter_ns": 0}
+                          "gather_ns": 0, "scatter_ns": 0, "submit_lag_ms": round(rst["replay_max_lag_ns"] * 1e-6, 3)}
                 else:
                     with ms.Server(ctx, ws, n, mode=mode_ids[name], copy_threads=args.copy_threads,
                                    waves_in_flight=args.waves_in_flight, idle_spin_us=args.idle_spin_us,
@@ -807,6 +807,7 @@ def serve_rows(args, rates, modes, seconds):
                          "p999_us": round(med["p999_us"], 1), "reps": len(reps),
                          "p99_us_each": [round(r["p99_us"], 1) for r in reps],
                          "p99_us_by_second": [r["by_sec"] for r in reps],
+                         "max_submit_lag_ms": [r["st"].get("submit_lag_ms") for r in reps],
                          "waves": st["waves"], "max_wave_requests": st["max_wave_requests"],
                          "conflict_waits": st["conflict_waits"], "budget_waits": st["budget_waits"],
                          "gather_s": round(st["gather_ns"] * 1e-9, 3), "scatter_s": round(st["scatter_ns"] * 1e-9, 3)})

@@ -559,6 +559,8 @@ typedef struct ms_resident_stats {
   uint64_t launches;         /* worker launches (first start and every restart) */
   uint64_t max_run_exits;    /* launches that ended by max_run_ms */
   uint64_t workers_running;  /* workers currently running */
+  uint64_t replay_max_lag_ns;  /* last ms_resident_replay: the largest delay between a request's
+                                  scheduled arrival and the submission of its last page */
 } ms_resident_stats;
 
 void ms_resident_config_default(ms_resident_config *cfg);

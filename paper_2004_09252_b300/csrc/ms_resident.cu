@@ -221,6 +221,7 @@ struct ms_resident {
   ms_resident_config cfg{};
   std::vector<Worker *> w;
   std::atomic<uint64_t> rr{0};
+  std::atomic<uint64_t> replay_max_lag_ns{0};
 };
 
 using namespace ms;
@@ -406,6 +407,7 @@ int ms_resident_get_stats(const ms_resident *r, ms_resident_stats *out) {
     out->max_run_exits += __atomic_load_n(&w->h_sh->timeouts, __ATOMIC_RELAXED);
     if (__atomic_load_n(&w->h_sh->state, __ATOMIC_ACQUIRE) == kRunning) out->workers_running += 1;
   }
+  out->replay_max_lag_ns = r->replay_max_lag_ns.load();
   return MS_OK;
 }
 
@@ -530,6 +532,7 @@ extern "C" int ms_resident_replay(ms_resident *r, void *host_base, uint64_t n_pa
     }
   });
   int rc = MS_OK;
+  uint64_t max_lag = 0;
   for (size_t q = 0; q < n && rc == MS_OK; ++q) {
     const uint64_t target = t0 + (uint64_t)(arrival_s[q] * 1e9);
     for (;;) {
@@ -570,7 +573,9 @@ extern "C" int ms_resident_replay(ms_resident *r, void *host_base, uint64_t n_pa
         published[w].store(idx + 1, std::memory_order_release);
       }
     }
+    if (rc == MS_OK) max_lag = std::max(max_lag, now_ns() - target);
   }
+  r->replay_max_lag_ns.store(max_lag);
   if (rc != MS_OK) err.store(rc);
   comp.join();
   if (rc != MS_OK) return rc;

@@ -153,7 +153,8 @@ class ms_resident_config(ctypes.Structure):
 
 
 class ms_resident_stats(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_uint64) for n in ("requests", "launches", "max_run_exits", "workers_running")]
+    _fields_ = [(n, ctypes.c_uint64) for n in ("requests", "launches", "max_run_exits", "workers_running",
+                                                "replay_max_lag_ns")]
 
 
 def _load():
