@@ -22,6 +22,8 @@ MS_OK, MS_EINVAL, MS_ENOTINIT, MS_ENOMEM, MS_ECUDA, MS_ETIMEDOUT, MS_EBUSY, MS_E
 MS_ESTARVED = -8
 MS_ENCRYPT, MS_DECRYPT = 0, 1
 MS_NOALLOC_MAX_PAGES = 16384
+MS_TICKETS = 4096
+MS_BATCH_MAX_CAPACITY = 1 << 26
 MS_FAULT_LAUNCH, MS_FAULT_COPY, MS_FAULT_GRAPH, MS_FAULT_SERVER = 1, 2, 4, 8
 
 PAGE_DTYPE = np.dtype([("addr", "<u8"), ("page_id", "<u8")])

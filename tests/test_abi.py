@@ -128,3 +128,23 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
     r = subprocess.run([sys.executable, "-c", "from paper_2004_09252_b300 import memshield"], cwd=tmp_path, env=env,
                        capture_output=True, text=True, timeout=120)
     assert r.returncode != 0 and "libmemshield.so not built" in r.stderr
+
+
+def test_constants_match_the_header():
+    """Every constant the binding mirrors has the header's value."""
+    from paper_2004_09252_b300 import memshield as m
+    names = ["MS_PAGE_BYTES", "MS_BLOCKS_PER_PAGE", "MS_KEY_BYTES", "MS_OK", "MS_EINVAL", "MS_ENOTINIT",
+             "MS_ENOMEM", "MS_ECUDA", "MS_ETIMEDOUT", "MS_EBUSY", "MS_ERANGE", "MS_ESTARVED", "MS_ENCRYPT",
+             "MS_DECRYPT", "MS_NOALLOC_MAX_PAGES", "MS_TICKETS", "MS_BATCH_MAX_CAPACITY", "MS_FAULT_LAUNCH",
+             "MS_FAULT_COPY", "MS_FAULT_GRAPH", "MS_FAULT_SERVER", "MS_SERVE_CONTINUOUS",
+             "MS_SERVE_ONE_PER_LAUNCH", "MS_SERVE_ZERO_COPY"]
+    src = ("#include <stdio.h>\n#include \"memshield.h\"\nint main(void) {\n"
+           + "".join(f'printf("%lld\\n", (long long)({n}));\n' for n in names) + "return 0;\n}\n")
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I", INCLUDE, c, "-o", exe])
+        got = [int(v) for v in subprocess.check_output([exe]).split()]
+    assert got == [getattr(m, n) for n in names]
+    assert len(m.PIPE_CLASSES) == 10
