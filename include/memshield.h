@@ -165,22 +165,27 @@ int ms_decrypt_pages_dev(ms_ctx *ctx, const ms_page *d_pages, size_t n);
 int ms_crypt_pages_dom(ms_ctx *ctx, const ms_page_dom *pages, size_t n);
 int ms_crypt_pages_dom_dev(ms_ctx *ctx, const ms_page_dom *d_pages, size_t n);
 
+/* The device address of pinned, mapped host memory (for page entries that the
+ * kernels read and write in place); MS_EINVAL for any other pointer.  The
+ * paper has no counterpart: its GPU module reaches the client's page through
+ * a buffer shared with the server (Sec. 4.4). */
+int ms_host_device_address(const void *host_ptr, uint64_t *dev_addr);
+
 /*
- * Ticketed submission (per-request completion, the fault path's need): the
- * host list `pages` (checked and copied as for ms_encrypt_pages; the page
- * addresses may be device memory or pinned, mapped host memory, which the
- * kernel then reads and writes in place over the host link) is queued as one
- * launch on the context's stream, and *ticket names it.  n = 0 gives a ticket
- * that completes after everything queued before it.  ms_poll: 1 done, 0
- * pending, < 0 error (MS_EINVAL for a ticket never issued).  ms_wait: MS_OK,
- * MS_ETIMEDOUT after timeout_ms, or an error.  At most MS_TICKETS
- * submissions may be pending: a submit whose ring slot still belongs to a
- * pending ticket returns MS_EBUSY (wait for older tickets first).
+ * Ticketed submission, Sec. 4.2-4.4: a faulting client stays stalled until
+ * the server has its page decrypted, so completion is per request, not per
+ * context.  The host list `pages` (checked and copied as for
+ * ms_encrypt_pages; the page addresses may be device memory or pinned,
+ * mapped host memory, which the kernel then reads and writes in place over
+ * the host link) is queued as one launch on the context's stream, and
+ * *ticket names it.  n = 0 gives a ticket that completes after everything
+ * queued before it.  ms_poll: 1 done, 0 pending, < 0 error (MS_EINVAL for a
+ * ticket never issued).  ms_wait: MS_OK, MS_ETIMEDOUT after timeout_ms, or an
+ * error.  At most MS_TICKETS submissions may be pending: a submit whose ring
+ * slot still belongs to a pending ticket returns MS_EBUSY (wait for older
+ * tickets first).
  */
 #define MS_TICKETS 4096
-/* The device address of pinned, mapped host memory (for page entries that the
- * kernels read and write in place); MS_EINVAL for any other pointer. */
-int ms_host_device_address(const void *host_ptr, uint64_t *dev_addr);
 int ms_submit_host(ms_ctx *ctx, int op, const ms_page *pages, size_t n, uint64_t *ticket);
 int ms_poll(ms_ctx *ctx, uint64_t ticket);
 int ms_wait(ms_ctx *ctx, uint64_t ticket, uint32_t timeout_ms);
@@ -194,25 +199,30 @@ int ms_wait(ms_ctx *ctx, uint64_t ticket, uint32_t timeout_ms);
 int ms_crypt_range(ms_ctx *ctx, int op, void *d_base, uint64_t first_page_id, size_t n_pages);
 
 /*
- * Wait, at most cfg.timeout_ms, until all work submitted on this context has
- * finished.  Returns MS_ETIMEDOUT if the bound ran out (the work is still
- * queued; call again), MS_EINVAL if a device-checked entry was bad since the
- * last ms_sync, MS_ESTARVED if a fed kernel gave up waiting, MS_ECUDA on a
- * CUDA error.  The context is held for the duration of the wait: other
- * threads' submissions on it wait too.  Threads that need completion of
- * their own requests without that use ms_submit_host and ms_wait.
+ * Sec. 4.2 and 4.4: the server resolves a client's page fault only once the
+ * GPU module has returned the decrypted page.  ms_sync waits, at most
+ * cfg.timeout_ms, until all work submitted on this context has finished.
+ * Returns MS_ETIMEDOUT if the bound ran out (the work is still queued; call
+ * again), MS_EINVAL if a device-checked entry was bad since the last
+ * ms_sync, MS_ESTARVED if a fed kernel gave up waiting, MS_ECUDA on a CUDA
+ * error.  The context is held for the duration of the wait: other threads'
+ * submissions on it wait too.  Threads that need completion of their own
+ * requests without that use ms_submit_host and ms_wait.
  */
 int ms_sync(ms_ctx *ctx);
-/* ms_sync with its own bound instead of cfg.timeout_ms (0 = only check). */
+/* ms_sync with its own bound instead of cfg.timeout_ms (0 = only check);
+ * Sec. 4.2 and 4.4, as ms_sync. */
 int ms_sync_for(ms_ctx *ctx, uint32_t timeout_ms);
 
 /*
- * Finish outstanding work (bounded), overwrite the device key with zeros and
- * free every resource.  ctx must not be used afterwards.  NULL is a no-op.
- * MS_EBUSY (and nothing is freed) while a batch, feed, server or resident
- * worker set created on the context has not been destroyed.  MS_ETIMEDOUT
- * (and nothing is touched: the context stays usable, call again) when the
- * queued work does not finish within timeout_ms.
+ * Sec. 4.4: the master key is kept only on the GPU (purged from the server's
+ * memory), so nothing of it may remain once the module ends.  ms_shutdown
+ * finishes outstanding work (bounded), overwrites the device key with zeros
+ * and frees every resource.  ctx must not be used afterwards.  NULL is a
+ * no-op.  MS_EBUSY (and nothing is freed) while a batch, feed, server or
+ * resident worker set created on the context has not been destroyed.
+ * MS_ETIMEDOUT (and nothing is touched: the context stays usable, call
+ * again) when the queued work does not finish within timeout_ms.
  */
 int ms_shutdown(ms_ctx *ctx);
 
@@ -252,7 +262,8 @@ typedef struct ms_shape {
 int ms_get_shape(const ms_ctx *ctx, ms_shape *out);
 int ms_set_shape(ms_ctx *ctx, const ms_shape *shape);
 
-/* Static English description of an ms_status code. */
+/* Static English description of an ms_status code.  The paper has no
+ * counterpart: it names no error conditions. */
 const char *ms_strerror(int code);
 
 /* The cudaError_t of the most recent MS_ECUDA on this context (0 if none). */

@@ -30,6 +30,27 @@ def test_header_declares_the_paper_calls():
         assert must in names
 
 
+BOUNDARY_CALLS = ("ms_init", "ms_encrypt_pages", "ms_decrypt_pages", "ms_sync", "ms_shutdown", "ms_strerror",
+                  "ms_submit_host", "ms_poll", "ms_wait")
+
+
+def comment_before(text, name):
+    """The last /* ... */ block that ends before the declaration of `name`."""
+    decl = re.search(r"^[a-z][^;{}()]*\b%s\s*\(" % name, text, flags=re.M)
+    assert decl, name
+    blocks = [m for m in re.finditer(r"/\*.*?\*/", text, flags=re.S) if m.end() <= decl.start()]
+    return blocks[-1].group(0) if blocks else ""
+
+
+def test_every_boundary_call_cites_its_passage():
+    """Each call of the path's boundary names the section of the paper that
+    defines it, or says that the paper has no counterpart."""
+    text = open(os.path.join(INCLUDE, "memshield.h")).read()
+    for name in BOUNDARY_CALLS:
+        c = " ".join(w for w in comment_before(text, name).split() if w not in ("/*", "*", "*/"))
+        assert re.search(r"Sec\. \d\.\d", c) or "paper has no counterpart" in c, (name, c)
+
+
 def test_library_exports_every_declared_symbol():
     from paper_2004_09252_b300 import memshield
     missing = [n for n in declared_functions() if not hasattr(memshield.lib, n)]
