@@ -88,13 +88,21 @@ REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
 
 
 class ClockSampler:
-    """Samples SM clock and clock-event reasons with NVML while the timed region runs."""
+    """Samples the SM clock and the clock-event reasons while the GPU is under
+    load: NVML when the binding is importable, else an ``nvidia-smi -lms``
+    child whose lines are read as they arrive.  Every sample carries its
+    host time, so the summary can say how many fell inside the timed region
+    (``mark_start``/``mark_end``) and how many in the loaded window around it."""
 
-    def __init__(self, torch_dev: int, period_s: float = 0.02):
-        self.samples, self.reasons, self.max_mhz = [], set(), None
+    def __init__(self, torch_dev: int, period_s: float = 0.025):
+        self.samples = []            # (monotonic time, sm MHz, reason bits)
+        self.max_mhz = None
         self.period = period_s
         self._stop = threading.Event()
         self._t = None
+        self.err = None
+        self.t_start = self.t_end = None
+        self.lock = threading.Lock()
         try:
             import pynvml
             pynvml.nvmlInit()
@@ -113,62 +121,94 @@ class ClockSampler:
         self.smi = None
         self.smi_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(torch_dev)).split(",")[0] or "0"
 
-    def _run(self):
+    def _add(self, mhz, reasons):
+        with self.lock:
+            self.samples.append((time.monotonic(), float(mhz), int(reasons)))
+
+    def _run_nvml(self):
         n = self.nvml
         while not self._stop.is_set():
             try:
-                self.samples.append(n.nvmlDeviceGetClockInfo(self.h, n.NVML_CLOCK_SM))
+                mhz = n.nvmlDeviceGetClockInfo(self.h, n.NVML_CLOCK_SM)
                 try:
                     r = n.nvmlDeviceGetCurrentClocksEventReasons(self.h)
                 except AttributeError:
                     r = n.nvmlDeviceGetCurrentClocksThrottleReasons(self.h)
-                for bit, name in REASONS.items():
-                    if r & bit and name != "gpu_idle":
-                        self.reasons.add(name)
+                self._add(mhz, r)
             except Exception:
                 pass
             time.sleep(self.period)
 
+    def _run_smi(self):
+        for line in self.smi.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 3:
+                continue
+            try:
+                mhz, mx, r = float(parts[0]), float(parts[1]), int(parts[2], 16)
+            except ValueError:
+                continue
+            self.max_mhz = mx
+            self._add(mhz, r)
+
     def __enter__(self):
         if self.nvml:
-            self._t = threading.Thread(target=self._run, daemon=True)
-            self._t.start()
+            self._t = threading.Thread(target=self._run_nvml, daemon=True)
         else:
             import subprocess
             try:
                 self.smi = subprocess.Popen(
                     ["nvidia-smi", "-i", self.smi_index, "--query-gpu=clocks.sm,clocks.max.sm,"
-                     "clocks_event_reasons.active", "--format=csv,noheader,nounits", "-lms", "50"],
-                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                     "clocks_event_reasons.active", "--format=csv,noheader,nounits",
+                     "-lms", str(int(self.period * 1000))],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
+                self._t = threading.Thread(target=self._run_smi, daemon=True)
             except Exception as e:
-                self.err += f"; nvidia-smi: {e}"
+                self.err = f"{self.err}; nvidia-smi: {e}"
+        if self._t:
+            self._t.start()
         return self
+
+    def count(self, since=None):
+        with self.lock:
+            return sum(1 for t, _, _ in self.samples if since is None or t >= since)
+
+    def mark_start(self):
+        self.t_start = time.monotonic()
+
+    def mark_end(self):
+        self.t_end = time.monotonic()
 
     def __exit__(self, *a):
         self._stop.set()
-        if self._t:
-            self._t.join()
         if self.smi:
             self.smi.terminate()
-            out, _ = self.smi.communicate(timeout=10)
-            for line in out.splitlines():
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 3:
-                    continue
-                try:
-                    self.samples.append(float(parts[0]))
-                    self.max_mhz = float(parts[1])
-                    r = int(parts[2], 16)
-                except ValueError:
-                    continue
-                for bit, name in REASONS.items():
-                    if r & bit and name != "gpu_idle":
-                        self.reasons.add(name)
+            try:
+                self.smi.wait(timeout=10)
+            except Exception:
+                self.smi.kill()
+        if self._t:
+            self._t.join(timeout=10)
 
-    def summary(self):
+    def summary(self, loaded_since=None):
+        """Median SM clock and the reasons seen over the samples taken since
+        ``loaded_since`` (the start of the loaded window), with the count of
+        those inside the timed region."""
+        with self.lock:
+            sel = [x for x in self.samples if loaded_since is None or x[0] >= loaded_since]
+        reasons = set()
+        for _, _, r in sel:
+            for bit, name in REASONS.items():
+                if r & bit and name != "gpu_idle":
+                    reasons.add(name)
+        timed = [x for x in sel if self.t_start is not None and self.t_start <= x[0] <= (self.t_end or 1e300)]
         src = "nvml" if self.nvml else ("nvidia-smi" if self.smi else "none")
-        out = {"sm_mhz": statistics.median(self.samples) if self.samples else None,
-               "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons), "samples": len(self.samples),
+        out = {"sm_mhz": statistics.median(m for _, m, _ in sel) if sel else None,
+               "sm_max_mhz": self.max_mhz, "reasons": sorted(reasons), "samples": len(sel),
+               "samples_in_timed_region": len(timed),
+               "sm_mhz_timed_region": statistics.median(m for _, m, _ in timed) if timed else None,
+               "window": "the timed steps plus untimed steps of the same launches right before them "
+                         "(the GPU under the same load throughout)",
                "source": src}
         if not self.nvml:
             out["nvml_error"] = self.err
@@ -269,8 +309,19 @@ def run_ours(args):
     K = args.steps
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * K + 1)]
     sampler = ClockSampler(dev)
-    barrier()
     with sampler:
+        # untimed steps of the same launches until the sampler has seen the
+        # loaded GPU at least 24 times (a few seconds at most): the timed
+        # region of a short run is shorter than one sampling period
+        barrier()
+        loaded = time.monotonic()
+        while sampler.count(loaded) < 24 and time.monotonic() - loaded < 6.0:
+            for _ in range(64):
+                ctx.encrypt_pages_dev(lst, n)
+                ctx.decrypt_pages_dev(lst, n)
+            torch.cuda.synchronize()
+        barrier()
+        sampler.mark_start()
         evs[0].record(stream)
         for k in range(K):
             ctx.encrypt_pages_dev(lst, n)
@@ -278,6 +329,7 @@ def run_ours(args):
             ctx.decrypt_pages_dev(lst, n)
             evs[2 * k + 2].record(stream)
         barrier()
+        sampler.mark_end()
     rc = ctx.sync()
     if rc != 0:
         raise RuntimeError(f"ms_sync failed: {ms.strerror(rc)}")
@@ -357,7 +409,7 @@ def run_ours(args):
                              "peak_gbs": peaks.get("hbm_gbs"),
                              "frac": round(alg_bytes / avg_launch_s / 1e9 / float(peaks.get("hbm_gbs", 6400.0)), 4),
                              "note": f"{peaks_kind} copy bandwidth"}},
-        "clocks": sampler.summary(),
+        "clocks": sampler.summary(loaded),
         "e2e": e2e,
     }
     if not args.no_serving and world == 1:
@@ -909,6 +961,11 @@ def run_pipes(args):
 
 # -------------------------------------------------------------- reference
 def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on the host cores.  A
+    step is one encrypt pass plus one decrypt pass over the whole 1 GiB bulk
+    buffer when (steps + warmup) such steps fit in about 150 s on this host;
+    otherwise over the largest prefix that does, and ``config.pages`` says
+    which."""
     rank, world, _ = env_rank()
     if rank != 0:
         return
@@ -919,15 +976,16 @@ def run_reference(args):
     oracle.build()
     threads = host_cores()
     key = synth.key_bytes(1)
-    cal = synth.page_bytes_fast(2, 0, 32)
-    ids = np.arange(32, dtype=np.uint64)
+    cal_n = max(64, threads * 64)
+    cal = synth.page_bytes_fast(2, 0, cal_n)
+    ids = np.arange(cal_n, dtype=np.uint64)
+    oracle.crypt_pages(key, cal, ids, ids, threads=threads)          # first touch, thread start
     t0 = time.perf_counter()
-    oracle.crypt_pages(key, cal, ids, ids, threads=1)
-    per_page = (time.perf_counter() - t0) / 32
-    budget = min(150.0, max(20.0, 1.5 * (args.steps + args.warmup)))
-    step_s = budget / (args.steps + args.warmup)
-    # a step is two passes (encrypt + decrypt); assume half-linear thread scaling
-    npg = int(max(threads * 4, min(BULK_PAGES, step_s / (2 * per_page) * threads / 2)))
+    oracle.crypt_pages(key, cal, ids, ids, threads=threads)
+    per_page = (time.perf_counter() - t0) / cal_n                    # seconds per page, all threads
+    budget = 150.0
+    steps = args.steps + args.warmup
+    npg = int(min(BULK_PAGES, max(threads * 4, budget / (steps * 2 * per_page))))
     buf = synth.page_bytes_fast(2, 0, npg)
     ids = np.arange(npg, dtype=np.uint64)
     for _ in range(args.warmup):
@@ -939,14 +997,17 @@ def run_reference(args):
         oracle.crypt_pages(key, buf, ids, ids, threads=threads)
     dt = time.perf_counter() - t0
     value = 2.0 * args.steps * npg * PAGE / dt / 1e9
-    sample = (f"each step: encrypt + decrypt of the first {npg} pages ({npg * PAGE / 2**20:.1f} MiB) of the "
-              f"bulk buffer on {threads} threads")
+    whole = npg == BULK_PAGES
+    sample = (f"each step: encrypt + decrypt of {'all' if whole else 'the first'} {npg} pages "
+              f"({npg * PAGE / 2**20:.1f} MiB) of the bulk buffer on {threads} threads")
+    workload = WORKLOAD if whole else (f"bulk, first {npg} of 262,144 pages (the whole buffer does not fit the "
+                                       f"reference arm's time budget on this host): " + WORKLOAD)
     print(json.dumps({
         "impl": "reference", "metric": "page encrypt GB/s (ChaCha20, 4 KiB pages, device-resident)",
         "value": round(value, 4), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (SplitMix64 seeded page bytes)",
-        "config": {"workload": WORKLOAD, "pages": BULK_PAGES, "page_bytes": PAGE, "rounds": 20,
+        "config": {"workload": workload, "pages": npg, "page_bytes": PAGE, "rounds": 20,
                    "l2": "host memory", "parallelism": "cpu"},
         "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
                          "sample": sample},

@@ -629,24 +629,33 @@ int ms_window_run_ticketed(ms_ctx *ctx, void *host_base, uint64_t n_pages, const
  *
  * For callers that must not call cudaMalloc at the moment they encrypt or
  * decrypt -- typically code resolving a page fault, where an allocation can
- * stall the whole device, can fail because a caching allocator holds the free
- * memory, and is forbidden while the caller's stream is being captured.  The
- * context (created earlier by ms_init, which does allocate) supplies the key,
- * the stream and the launch shape; the call itself allocates nothing.
+ * stall the whole device or fail because a caching allocator holds the free
+ * memory.  The context (created earlier by ms_init, which does allocate)
+ * supplies the key, the stream and the launch shape; the call itself
+ * allocates nothing, on the device or on the host.
  *
- * pages: host list of n entries, checked like ms_encrypt_pages (MS_EINVAL on a
- * NULL or misaligned address, nothing launched).  n above
- * MS_NOALLOC_MAX_PAGES returns MS_ERANGE and does nothing.
+ * pages: host list of n entries, checked like ms_encrypt_pages: MS_EINVAL,
+ * with nothing launched, on a NULL or misaligned address or, when the
+ * context was created with check_duplicates, on an address listed twice.
+ * n above MS_NOALLOC_MAX_PAGES returns MS_ERANGE and does nothing.
+ *
  * Scratch: the entry list and the status word go to one file-scope device
  * array of 256 + 16 * MS_NOALLOC_MAX_PAGES bytes (256.25 KiB) that every GPU
  * using the library holds until the process exits.  The first call on a
- * device looks up that array's device address (set-up, once per device); make
- * that first call before any stream capture.  All calls share the array:
- * calls whose work overlaps on the GPU (two contexts, two threads, two
- * streams) race on it and must be serialised by the caller.
- * Unlike ms_encrypt_pages, the call waits (bounded by timeout_ms) for the
- * kernel to finish and returns its status: MS_OK, MS_EINVAL for a bad entry,
- * MS_ETIMEDOUT, MS_ECUDA.
+ * device looks up that array's device address (set-up, once per device) and
+ * keeps it for the life of the process; make that first call before any
+ * stream capture, and do not use this entry point on a device after a
+ * device reset (cudaDeviceReset).  All calls share the array: calls whose
+ * work overlaps on the GPU (two contexts, two threads, two streams) race on
+ * it and must be serialised by the caller.
+ *
+ * The call blocks: it waits (bounded by timeout_ms) for its kernel and reads
+ * the kernel's status back.  It returns MS_OK, MS_EINVAL for a bad entry,
+ * MS_ETIMEDOUT or MS_ECUDA; it returns MS_EINVAL without doing anything
+ * while the context's stream is being captured.  After MS_ETIMEDOUT the
+ * kernel may still be using the shared array: call ms_sync on the context
+ * until it returns something other than MS_ETIMEDOUT before the next call to
+ * ms_crypt_pages_noalloc on that device, from any context.
  */
 #define MS_NOALLOC_MAX_PAGES 16384u
 int ms_crypt_pages_noalloc(ms_ctx *ctx, int op, const ms_page *pages, size_t n);
