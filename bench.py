@@ -872,7 +872,9 @@ def serve_rows(args, rates, modes, seconds):
 # ------------------------------------------- sliding-window clients (NEXT)
 def run_window(args):
     """Clients fault through FIFO windows of clear pages (Sec. 4.3), as in the
-    paper's Table 1 (window 4..32 pages) and Table 2 (1, 2, 4 instances)."""
+    paper's Table 1 (window 4..32 pages) and Table 2 (1, 2, 4 instances), with
+    background eviction off (0) and on (the free-slot thresholds of
+    --window-free, the paper's proposed improvement)."""
     import numpy as np
     import torch
 
@@ -900,33 +902,39 @@ def run_window(args):
             for n_cl in args.window_clients:
                 for wnd in args.window_sizes:
                     for batch in args.window_batches:
-                        if batch > wnd + 1:
-                            continue
-                        # clients resume from where the previous run left their windows: re-encrypt them first
-                        for c, win in state.items():
-                            if win:
-                                srv.wait(srv.submit(ms.MS_ENCRYPT, np.array(win), domain=1000 + c), 20000)
-                        state = {}
-                        cl = [(1000 + c, c * per, per, traces[c]) for c in range(n_cl)]
-                        t0 = time.perf_counter()
-                        if backend == "ticketed":   # one clone of ctx per client: its PID, its stream
-                            st, wins = ctx.run_window_clients(ws, n, wnd, batch, cl, timeout_ms=20000)
-                        elif backend == "resident":
-                            st, wins = res.run_window_clients(ws, n, wnd, batch, cl, timeout_ms=20000)
-                        else:
-                            st, wins = srv.run_window_clients(wnd, batch, cl, timeout_ms=20000)
-                        el = time.perf_counter() - t0
-                        state = {c: wins[c] for c in range(n_cl)}
-                        faults = sum(x["faults"] for x in st)
-                        rows.append({"backend": backend, "clients": n_cl, "window_pages": wnd, "evict_batch": batch,
-                                     "accesses": sum(x["accesses"] for x in st), "faults": faults,
-                                     "evictions": sum(x["evictions"] for x in st),
-                                     "evict_requests": sum(x["evict_requests"] for x in st),
-                                     "faults_per_s": round(faults / el, 1),
-                                     "fault_p50_us": round(float(np.mean([x["fault_p50_us"] for x in st])), 1),
-                                     "fault_p99_us": round(float(max(x["fault_p99_us"] for x in st)), 1),
-                                     "client_s_max": round(max(x["elapsed_s"] for x in st), 3)})
-                        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+                        for free in args.window_free:
+                            if batch > wnd + 1 or free >= wnd:
+                                continue
+                            # clients resume from where the previous run left their windows: re-encrypt them first
+                            for c, win in state.items():
+                                if win:
+                                    srv.wait(srv.submit(ms.MS_ENCRYPT, np.array(win), domain=1000 + c), 20000)
+                            state = {}
+                            cl = [(1000 + c, c * per, per, traces[c]) for c in range(n_cl)]
+                            t0 = time.perf_counter()
+                            if backend == "ticketed":   # one clone of ctx per client: its PID, its stream
+                                st, wins = ctx.run_window_clients(ws, n, wnd, batch, cl, timeout_ms=20000,
+                                                                  background_free=free)
+                            elif backend == "resident":
+                                st, wins = res.run_window_clients(ws, n, wnd, batch, cl, timeout_ms=20000,
+                                                                  background_free=free)
+                            else:
+                                st, wins = srv.run_window_clients(wnd, batch, cl, timeout_ms=20000,
+                                                                  background_free=free)
+                            el = time.perf_counter() - t0
+                            state = {c: wins[c] for c in range(n_cl)}
+                            faults = sum(x["faults"] for x in st)
+                            rows.append({"backend": backend, "clients": n_cl, "window_pages": wnd,
+                                         "evict_batch": batch, "background_free": free,
+                                         "accesses": sum(x["accesses"] for x in st), "faults": faults,
+                                         "evictions": sum(x["evictions"] for x in st),
+                                         "evict_requests": sum(x["evict_requests"] for x in st),
+                                         "background_evictions": sum(x["background_evictions"] for x in st),
+                                         "faults_per_s": round(faults / el, 1),
+                                         "fault_p50_us": round(float(np.mean([x["fault_p50_us"] for x in st])), 1),
+                                         "fault_p99_us": round(float(max(x["fault_p99_us"] for x in st)), 1),
+                                         "client_s_max": round(max(x["elapsed_s"] for x in st), 3)})
+                            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     finally:
         if res is not None:
             res.destroy()
@@ -1048,6 +1056,8 @@ def main():
     ap.add_argument("--window-clients", type=lambda v: [int(x) for x in v.split(",")], default=[1, 2, 4])
     ap.add_argument("--window-sizes", type=lambda v: [int(x) for x in v.split(",")], default=[4, 8, 16, 32])
     ap.add_argument("--window-batches", type=lambda v: [int(x) for x in v.split(",")], default=[1, 8])
+    ap.add_argument("--window-free", type=lambda v: [int(x) for x in v.split(",")], default=[0, 1],
+                    help="background eviction thresholds: free window slots the evictor keeps (0 = off)")
     ap.add_argument("--window-backends", type=lambda v: v.split(","), default=["server", "resident", "ticketed"],
                     help="serve the window clients through the staged server, resident workers and/or "
                          "ticketed launches")

@@ -505,14 +505,26 @@ int ms_server_get_stats(const ms_server *srv, ms_server_stats *out);
  *   - when the window holds more than window_pages pages, its oldest
  *     evict_batch pages are encrypted by one request the client does not
  *     wait for (evict_batch = 1 is the paper's policy; larger batches evict
- *     ahead of need, as the paper's future work suggests).
+ *     ahead of need).
+ * Background eviction (the paper's conclusions, Sec. 7, propose encrypting
+ * window pages in the background once the number of free slots drops below
+ * a threshold): with background_free = T (1 .. window_pages - 1) each client
+ * also runs an evictor thread.  Whenever fewer than T of the window's
+ * window_pages slots are free, the evictor encrypts the oldest clear pages
+ * (requests of at most evict_batch pages) until T slots are free again, off
+ * the faulting thread's path; the overflow rule above stays as the fallback
+ * when the evictor runs behind.  Client and evictor share the window under
+ * one lock; a page's eviction is always submitted before any later fault on
+ * it, and a faulting page joins the window only once it is decrypted.
  * Each client runs on its own thread; its requests use its domain (PID).
  * At the end every eviction has completed; the pages still in a client's
  * window are in clear and all its other pages are encrypted.
  */
 typedef struct ms_window_config {
-  uint32_t window_pages;  /* maximum pages in clear per client (Table 1: 4, 8, 16, 32) */
-  uint32_t evict_batch;   /* pages encrypted per eviction request, 1..window_pages + 1 */
+  uint32_t window_pages;     /* maximum pages in clear per client (Table 1: 4, 8, 16, 32) */
+  uint32_t evict_batch;      /* pages encrypted per eviction request, 1..window_pages + 1 */
+  uint32_t background_free;  /* 0: no background eviction; else T, 1..window_pages - 1 (above) */
+  uint32_t reserved;         /* must be 0 */
 } ms_window_config;
 
 typedef struct ms_window_client {
@@ -525,10 +537,12 @@ typedef struct ms_window_client {
 } ms_window_client;
 
 typedef struct ms_window_stats {
-  uint64_t accesses, hits, faults, evictions, evict_requests;
+  uint64_t accesses, hits, faults, evictions, evict_requests;  /* evictions: pages, both paths */
   uint64_t final_window_pages;
   double fault_p50_us, fault_p99_us, fault_max_us;  /* fault service time seen by the client */
   double elapsed_s;                                 /* the client's whole trace */
+  uint64_t background_evictions;                    /* pages encrypted by the background evictor */
+  uint64_t background_requests;                     /* its requests */
 } ms_window_stats;
 
 /* Run the clients to the end of their traces.  stats_out (may be NULL) gets one

@@ -12,45 +12,56 @@
 // which the client does not wait for (a later fault on one of those pages
 // waits for its encryption through the server's in-flight rule).  Clients
 // run on their own threads with their own domain (the paper's PID).
+//
+// Background eviction (the paper's conclusions propose starting to encrypt
+// window pages in the background once the free slots drop below a
+// threshold): with background_free = T > 0 every client also gets an
+// evictor thread.  Whenever fewer than T of the window's slots are free, the
+// evictor encrypts the oldest clear pages until T are free again, so the
+// faulting thread only decrypts.  The client and its evictor share the
+// window under one lock, and every request that touches a page is submitted
+// under that lock, so each backend sees a page's eviction before any later
+// fault on it (the server's in-flight rule, a resident wait on the eviction's
+// ticket, or the clone's stream order then keep them apart on the GPU).  A
+// faulting page joins the window only once its decryption has completed,
+// so the evictor never picks a page whose fault is still running.
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <mutex>
 #include <thread>
 #include <unordered_set>
 #include <vector>
 
 #include "ms_internal.h"
+#include "ms_window_client.h"
 
 namespace {
 
 using clk = std::chrono::steady_clock;
+using ms::window::ClientRun;
+using ms::window::percentile;
+using ms::window::run_client;
 
-struct ClientRun {
-  const ms_window_client *cl;
-  ms_window_stats st{};
-  std::vector<double> lat_us;
-  std::vector<uint64_t> final_window;
-  int rc = MS_OK;
-};
-
-// Where a client's requests go.  Fault: decrypt one page and wait for it.
-// Evict: encrypt pages without waiting.  Drain: wait for every eviction.
+// Where a client's requests go.  fault_submit / fault_wait: decrypt one page
+// and wait for it.  evict: encrypt pages without waiting.  drain: wait for
+// every eviction.  fault_submit and evict are called under the client's
+// window lock; fault_wait without it.
 struct ServerBackend {
   ms_server *srv;
   uint32_t timeout_ms;
   std::vector<uint64_t> evict_tickets;
-  int fault(uint32_t domain, uint64_t pg) {
-    uint64_t ticket;
-    int rc;
+  int fault_submit(uint32_t domain, uint64_t pg, uint64_t *ticket) {
+    // an eviction of this page still in flight is waited for by the server's in-flight rule
     for (;;) {
-      rc = ms_server_submit_dom(srv, MS_DECRYPT, domain, &pg, 1, &ticket);
-      if (rc != MS_EBUSY) break;
+      const int rc = ms_server_submit_dom(srv, MS_DECRYPT, domain, &pg, 1, ticket);
+      if (rc != MS_EBUSY) return rc;
       std::this_thread::yield();
     }
-    // an eviction of this page still in flight is waited for by the server's in-flight rule
-    return rc == MS_OK ? ms_server_wait(srv, ticket, timeout_ms) : rc;
   }
+  int fault_wait(uint64_t ticket) { return ms_server_wait(srv, ticket, timeout_ms); }
   int evict(uint32_t domain, const uint64_t *pages, size_t k) {
     uint64_t ticket;
     int rc;
@@ -91,18 +102,16 @@ struct ResidentBackend {
       std::this_thread::yield();
     }
   }
-  int fault(uint32_t domain, uint64_t pg) {
+  int fault_submit(uint32_t domain, uint64_t pg, uint64_t *ticket) {
     uint64_t &last = last_ticket[pg - first_page];
     if (last != ~0ull) {  // its eviction may still be running: a page is never in flight twice
       const int rc = ms_resident_wait(res, last, timeout_ms);
       if (rc != MS_OK) return rc;
+      last = ~0ull;
     }
-    uint64_t ticket;
-    int rc = submit(domain, pg, &ticket);
-    if (rc == MS_OK) rc = ms_resident_wait(res, ticket, timeout_ms);
-    last = ~0ull;
-    return rc;
+    return submit(domain, pg, ticket);
   }
+  int fault_wait(uint64_t ticket) { return ms_resident_wait(res, ticket, timeout_ms); }
   int evict(uint32_t domain, const uint64_t *pages, size_t k) {
     for (size_t i = 0; i < k; ++i) {
       uint64_t ticket;
@@ -145,11 +154,8 @@ struct TicketBackend {
       std::this_thread::yield();
     }
   }
-  int fault(uint32_t, uint64_t pg) {
-    uint64_t t;
-    const int rc = submit(&pg, 1, &t, MS_DECRYPT);
-    return rc == MS_OK ? ms_wait(ctx, t, timeout_ms) : rc;
-  }
+  int fault_submit(uint32_t, uint64_t pg, uint64_t *ticket) { return submit(&pg, 1, ticket, MS_DECRYPT); }
+  int fault_wait(uint64_t ticket) { return ms_wait(ctx, ticket, timeout_ms); }
   int evict(uint32_t, const uint64_t *pages, size_t k) {
     uint64_t t;
     const int rc = submit(pages, k, &t, MS_ENCRYPT);
@@ -159,73 +165,11 @@ struct TicketBackend {
   int drain() { return last_evict == ~0ull ? MS_OK : ms_wait(ctx, last_evict, timeout_ms); }
 };
 
-template <typename Backend>
-void run_client(Backend &be, const ms_window_config &cfg, ClientRun &cr) {
-  const ms_window_client &cl = *cr.cl;
-  std::deque<uint64_t> window;  // working-set page indices in clear, oldest first
-  std::unordered_set<uint64_t> in_window;
-  cr.lat_us.reserve(cl.trace_len / 4 + 16);
-  const auto t0 = clk::now();
-  for (size_t i = 0; i < cl.trace_len; ++i) {
-    const uint64_t rel = cl.trace[i];
-    if (rel >= cl.n_pages) {
-      cr.rc = MS_EINVAL;
-      return;
-    }
-    const uint64_t pg = cl.first_page + rel;
-    cr.st.accesses += 1;
-    if (in_window.count(pg)) {
-      cr.st.hits += 1;
-      continue;
-    }
-    // fault: decrypt the page and wait for it
-    const auto f0 = clk::now();
-    int rc = be.fault(cl.domain, pg);
-    if (rc != MS_OK) {
-      cr.rc = rc;
-      return;
-    }
-    cr.lat_us.push_back(std::chrono::duration<double, std::micro>(clk::now() - f0).count());
-    cr.st.faults += 1;
-    window.push_back(pg);
-    in_window.insert(pg);
-    if (window.size() > cfg.window_pages) {
-      const size_t k = std::min<size_t>(cfg.evict_batch, window.size());
-      std::vector<uint64_t> ev(window.begin(), window.begin() + (long)k);
-      window.erase(window.begin(), window.begin() + (long)k);
-      for (uint64_t e : ev) in_window.erase(e);
-      rc = be.evict(cl.domain, ev.data(), k);
-      if (rc != MS_OK) {
-        cr.rc = rc;
-        return;
-      }
-      cr.st.evictions += k;
-      cr.st.evict_requests += 1;
-    }
-  }
-  // the client's evictions complete before it reports
-  const int rc = be.drain();
-  if (rc != MS_OK) {
-    cr.rc = rc;
-    return;
-  }
-  cr.st.elapsed_s = std::chrono::duration<double>(clk::now() - t0).count();
-  cr.final_window.assign(window.begin(), window.end());
-}
-
-double percentile(std::vector<double> v, double q) {
-  if (v.empty()) return 0.0;
-  std::sort(v.begin(), v.end());
-  const double pos = q * (double)(v.size() - 1);
-  const size_t lo = (size_t)pos;
-  const size_t hi = std::min(v.size() - 1, lo + 1);
-  return v[lo] + (v[hi] - v[lo]) * (pos - (double)lo);
-}
-
 int check_window_args(const ms_window_config *cfg, const ms_window_client *clients, size_t n_clients,
                       uint64_t n_pages) {
   if (!cfg || (n_clients && !clients)) return MS_EINVAL;
   if (cfg->window_pages == 0 || cfg->evict_batch == 0 || cfg->evict_batch > cfg->window_pages + 1) return MS_EINVAL;
+  if (cfg->background_free >= cfg->window_pages || cfg->reserved) return MS_EINVAL;
   for (size_t c = 0; c < n_clients; ++c) {
     if (!clients[c].trace && clients[c].trace_len) return MS_EINVAL;
     if (clients[c].first_page > n_pages || clients[c].n_pages > n_pages - clients[c].first_page) return MS_EINVAL;

@@ -118,7 +118,8 @@ MS_SERVE_CONTINUOUS, MS_SERVE_ONE_PER_LAUNCH, MS_SERVE_ZERO_COPY = 0, 1, 2
 
 
 class ms_window_config(ctypes.Structure):
-    _fields_ = [("window_pages", ctypes.c_uint32), ("evict_batch", ctypes.c_uint32)]
+    _fields_ = [("window_pages", ctypes.c_uint32), ("evict_batch", ctypes.c_uint32),
+                ("background_free", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class ms_window_client(ctypes.Structure):
@@ -129,7 +130,8 @@ class ms_window_client(ctypes.Structure):
 class ms_window_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("accesses", "hits", "faults", "evictions", "evict_requests",
                                                "final_window_pages")] + \
-               [(n, ctypes.c_double) for n in ("fault_p50_us", "fault_p99_us", "fault_max_us", "elapsed_s")]
+               [(n, ctypes.c_double) for n in ("fault_p50_us", "fault_p99_us", "fault_max_us", "elapsed_s")] + \
+               [(n, ctypes.c_uint64) for n in ("background_evictions", "background_requests")]
 
 
 class ms_feed_config(ctypes.Structure):
@@ -425,14 +427,14 @@ class Context:
         _check(_lib.ms_wait(self.handle, ticket, timeout_ms), "ms_wait")
 
     def run_window_clients(self, host_base, n_pages: int, window_pages: int, evict_batch: int, clients,
-                           timeout_ms: int = 60000):
+                           timeout_ms: int = 60000, background_free: int = 0):
         """Sliding-window clients served by ticketed launches, one clone of this
         context per client (its domain, its stream), in place on a pinned, mapped
         working set."""
         base = _ptr(host_base)
         return _run_window(lambda cfg, arr, n, st, fw: _lib.ms_window_run_ticketed(
             self.handle, base, n_pages, cfg, arr, n, st, fw, timeout_ms),
-            "ms_window_run_ticketed", window_pages, evict_batch, clients)
+            "ms_window_run_ticketed", window_pages, evict_batch, clients, background_free)
 
     def feed(self, capacity: int = 0, chunk: int = 0, wait_ms: int = 0, grab: int = 0) -> "Feed":
         return Feed(self, capacity, chunk, wait_ms, grab)
@@ -676,11 +678,14 @@ class Server:
                                      ctypes.byref(mk), timeout_ms), "ms_server_replay")
         return lat, mk.value
 
-    def run_window_clients(self, window_pages: int, evict_batch: int, clients, timeout_ms: int = 60000):
+    def run_window_clients(self, window_pages: int, evict_batch: int, clients, timeout_ms: int = 60000,
+                           background_free: int = 0):
         """Sliding-window clients: `clients` is a list of (domain, first_page, n_pages, trace).
-        Returns (per-client stats dicts, per-client final windows as lists of page indices)."""
+        background_free = T > 0 adds a background evictor per client that keeps T
+        window slots free.  Returns (per-client stats dicts, per-client final
+        windows as lists of page indices)."""
         return _run_window(lambda cfg, arr, n, st, fw: _lib.ms_window_run(self.handle, cfg, arr, n, st, fw, timeout_ms),
-                           "ms_window_run", window_pages, evict_batch, clients)
+                           "ms_window_run", window_pages, evict_batch, clients, background_free)
 
     def stats(self) -> dict:
         st = ms_server_stats()
@@ -702,8 +707,8 @@ class Server:
         self.destroy()
 
 
-def _run_window(call, name: str, window_pages: int, evict_batch: int, clients):
-    cfg = ms_window_config(window_pages, evict_batch)
+def _run_window(call, name: str, window_pages: int, evict_batch: int, clients, background_free: int = 0):
+    cfg = ms_window_config(window_pages, evict_batch, background_free, 0)
     arr = (ms_window_client * len(clients))()
     keep = []
     for i, (dom, first, n, trace) in enumerate(clients):
@@ -776,13 +781,13 @@ class Resident:
         return lat, mk.value
 
     def run_window_clients(self, host_base, n_pages: int, window_pages: int, evict_batch: int, clients,
-                           timeout_ms: int = 60000):
+                           timeout_ms: int = 60000, background_free: int = 0):
         """The sliding-window clients of Server.run_window_clients, served by these
         workers in place on a pinned, mapped working set of n_pages pages."""
         base = _ptr(host_base)
         return _run_window(lambda cfg, arr, n, st, fw: _lib.ms_window_run_resident(
             self.handle, base, n_pages, cfg, arr, n, st, fw, timeout_ms),
-            "ms_window_run_resident", window_pages, evict_batch, clients)
+            "ms_window_run_resident", window_pages, evict_batch, clients, background_free)
 
     def destroy(self) -> int:
         if self.handle:

@@ -238,3 +238,54 @@ def test_batched_form_with_per_page_domains(ms, key1, use_graph):
             with pytest.raises(ms.MemShieldError):
                 plain_batch.add_dom(ms.MS_ENCRYPT, ms.pages_dom_array([d.data_ptr()], [0], [1]))
     assert np.array_equal(d.cpu().numpy(), oracle_by_domain(key1, plain, slots, slots, doms))
+
+
+@pytest.mark.parametrize("backend", ["server", "resident", "ticketed"])
+@pytest.mark.parametrize("window,batch,free", [(4, 1, 1), (8, 1, 3), (16, 4, 6), (32, 8, 31)])
+def test_background_eviction_final_state(ms, key1, backend, window, batch, free):
+    """Background eviction (the paper's conclusions: encrypt window pages ahead
+    of need once the free slots fall below a threshold): every client's
+    evictor keeps `free` window slots free off the fault path.  Afterwards the
+    final-window pages are in clear and every other page of the client is
+    encrypted under its PID (the oracle); the final window holds at most
+    window - free pages and the evictor did run."""
+    per, n_clients = 128, 3
+    n = per * n_clients
+    plain = synth.page_bytes_fast(396, 0, n)
+    h = torch.from_numpy(plain.copy()).pin_memory()
+    doms = [701, 702, 703]
+    clients = [(doms[c], c * per, per, synth.window_trace(397 + c, per, 1500)) for c in range(n_clients)]
+    with ms.Context(key1) as ctx:
+        with ms.Server(ctx, h, n) as srv:
+            for c in range(n_clients):             # every client page starts encrypted
+                srv.wait(srv.submit(ms.MS_ENCRYPT, np.arange(c * per, (c + 1) * per), domain=doms[c]))
+            if backend == "server":
+                stats, wins = srv.run_window_clients(window, batch, clients, background_free=free)
+        if backend == "resident":
+            with ms.Resident(ctx, workers=4) as res:
+                stats, wins = res.run_window_clients(h, n, window, batch, clients, background_free=free)
+        elif backend == "ticketed":
+            stats, wins = ctx.run_window_clients(h, n, window, batch, clients, background_free=free)
+    ws = h.numpy()
+    for c in range(n_clients):
+        st, win = stats[c], wins[c]
+        assert st["accesses"] == 1500 and st["hits"] + st["faults"] == 1500
+        assert st["faults"] - st["evictions"] == len(win) == st["final_window_pages"] <= window - free
+        assert 0 < st["background_evictions"] <= st["evictions"]
+        assert 0 < st["background_requests"] <= st["evict_requests"]
+        assert len(set(win)) == len(win) and all(c * per <= p < (c + 1) * per for p in win)
+        enc = np.array(sorted(set(range(c * per, (c + 1) * per)) - set(win)), dtype=np.uint64)
+        want = plain[c * per * PAGE:(c + 1) * per * PAGE].copy()
+        oracle.crypt_pages(key1, want, enc - np.uint64(c * per), enc, domain=doms[c])
+        assert np.array_equal(ws[c * per * PAGE:(c + 1) * per * PAGE], want), f"client {c}"
+
+
+def test_background_eviction_rejects_bad_thresholds(ms, key1):
+    n = 64
+    h = torch.from_numpy(synth.page_bytes(399, 0, n)).pin_memory()
+    tr = np.zeros(4, dtype=np.uint64)
+    with ms.Context(key1) as ctx, ms.Server(ctx, h, n) as srv:
+        for free in (4, 9):                         # the threshold must leave room for a page
+            with pytest.raises(ms.MemShieldError) as e:
+                srv.run_window_clients(4, 1, [(1, 0, 32, tr)], background_free=free)
+            assert e.value.code == ms.MS_EINVAL
