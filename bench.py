@@ -348,28 +348,36 @@ def run_ours(args):
     alg_bytes = n * (2 * PAGE + 16)
     traffic = profiled_traffic() if n == BULK_PAGES else None  # the capture is of the 1 GiB launch
 
-    # e2e through the host-page entry point (pinned host memory, copies timed)
+    # e2e through the host-page entry point on the host-page workload: a 4 GiB
+    # pinned host buffer (seed 4), copies inside the timed region, beside the
+    # host link measured in the same run
     e2e = None
     if not args.no_e2e:
-        hbuf = torch.empty(n * PAGE, dtype=torch.uint8).pin_memory()
-        synth.fill_pages(hbuf.data_ptr(), 2, 0, n)
+        ne = args.e2e_pages
+        hbuf = torch.empty(ne * PAGE, dtype=torch.uint8).pin_memory()
+        synth.fill_pages(hbuf.data_ptr(), 4, 0, ne)
+        head = hbuf[:PAGE * 64].clone()
+        link = host_link(hbuf)
         chunk = args.e2e_chunk_mib << 20
-        ctx.crypt_host(ms.MS_ENCRYPT, hbuf, 0, n, chunk, args.e2e_streams)
-        ctx.crypt_host(ms.MS_DECRYPT, hbuf, 0, n, chunk, args.e2e_streams)
+        ctx.crypt_host(ms.MS_ENCRYPT, hbuf, 0, ne, chunk, args.e2e_streams)
+        ctx.crypt_host(ms.MS_DECRYPT, hbuf, 0, ne, chunk, args.e2e_streams)
         es = max(2, min(5, K))
         barrier()
         t0 = time.perf_counter()
         for _ in range(es):
-            ctx.crypt_host(ms.MS_ENCRYPT, hbuf, 0, n, chunk, args.e2e_streams)
-            ctx.crypt_host(ms.MS_DECRYPT, hbuf, 0, n, chunk, args.e2e_streams)
+            ctx.crypt_host(ms.MS_ENCRYPT, hbuf, 0, ne, chunk, args.e2e_streams)
+            ctx.crypt_host(ms.MS_DECRYPT, hbuf, 0, ne, chunk, args.e2e_streams)
         barrier()
-        el_ms, e2e_gbs = aggregate_replicas((time.perf_counter() - t0) * 1e3, 2.0 * es * n * PAGE, world,
+        el_ms, e2e_gbs = aggregate_replicas((time.perf_counter() - t0) * 1e3, 2.0 * es * ne * PAGE, world,
                                             d.device)
-        ok = np.array_equal(hbuf[:PAGE * 16].numpy(), plain[:PAGE * 16])
+        ok = torch.equal(hbuf[:PAGE * 64], head)
         e2e = {"value": round(e2e_gbs, 3), "unit": "GB/s",
-               "h2d_bytes_per_step": 2 * n * PAGE, "d2h_bytes_per_step": 2 * n * PAGE,
+               "h2d_bytes_per_step": 2 * ne * PAGE, "d2h_bytes_per_step": 2 * ne * PAGE,
+               "workload": (f"host pages: {ne * PAGE / 2**30:g} GiB pinned host buffer ({ne} pages, SplitMix64 "
+                            "seed 4), ids 0.., through ms_crypt_host; a step = one encrypt pass + one decrypt pass"),
                "steps": es, "chunk_bytes": chunk, "streams": args.e2e_streams or 2,
-               "host_memory": "pinned", "round_trip_ok": bool(ok)}
+               "host_memory": "pinned", "round_trip_ok": bool(ok),
+               "link": link, "frac_of_link": round(e2e_gbs / world / link["bound_gbs"], 3)}
         del hbuf
 
     ctx.shutdown()
@@ -412,12 +420,42 @@ def run_ours(args):
         "clocks": sampler.summary(loaded),
         "e2e": e2e,
     }
+    if not args.no_batching and world == 1:
+        # the batching workload at full size: one launch per request, graph-launched
+        # submits (doubling from 60 to 4000 requests) and the fed form
+        br = batching_result(args, ["r60-4000"], [16384])
+        fed = next(r for r in br["batched"] if str(r["requests_per_submit"]).startswith("fed"))
+        graph = next(r for r in br["batched"] if not str(r["requests_per_submit"]).startswith("fed"))
+        keys = ("pages_per_s", "gb_per_s", "gpu_span_ms", "wall_s", "identical_to_one_launch_per_request")
+        line["batching"] = {
+            "workload": br["config"]["workload"], "unit": "pages/s",
+            "one_launch_per_request": br["one_launch_per_request"],
+            "graph_launched": dict({k: graph[k] for k in keys}, submits=graph["submits"],
+                                   requests_per_submit=graph["requests_per_submit"]),
+            "fed": dict({k: fed[k] for k in keys}, publications=fed["publications"]),
+            "speedup_vs_one_launch_per_request": br["speedup_vs_one_launch_per_request"],
+            "autotune": br["autotune"]}
     if not args.no_serving and world == 1:
-        rows, _ = serve_rows(args, [1.41e5, 2e6], ["continuous", "one_per_launch", "resident"], 2.0)
+        rows, setup_s = serve_rows(args, args.serve_rates, ["continuous", "one_per_launch", "resident"],
+                                   args.serve_seconds, one_per_launch_cap=args.one_per_launch_cap)
+        keep = ("offered_pages_per_s", "mode", "requests", "arrival_s", "sustained_pages_per_s", "p50_us", "p99_us",
+                "p999_us", "first_second", "steady", "p99_us_by_second", "max_submit_lag_ms")
+        one = {r["offered_pages_per_s"]: r for r in rows if r["mode"] == "one_per_launch"}
+
+        def p99(r):  # the steady state where the run has one, else the whole run
+            return r["steady"]["p99_us"] if r.get("steady") else r["p99_us"]
         line["serving"] = {
-            "workload": SERVE_WORKLOAD.format(n=args.serve_pages, gib=args.serve_pages * PAGE / 2**30, sec=2.0),
-            "rows": [{k: r[k] for k in ("offered_pages_per_s", "mode", "sustained_pages_per_s", "p50_us", "p99_us",
-                                        "p999_us")} for r in rows]}
+            "workload": SERVE_WORKLOAD.format(n=args.serve_pages, gib=args.serve_pages * PAGE / 2**30,
+                                              sec=args.serve_seconds)
+            + f"; one launch per request capped at {args.one_per_launch_cap} requests (>= 50k requests)"
+            + (f"; {args.serve_warmup_s:g} s of separate requests replayed untimed before each run"
+               if args.serve_warmup_s > 0 else ""),
+            "working_set_setup_s": round(setup_s, 1),
+            "rows": [{k: r[k] for k in keep} for r in rows],
+            "vs_one_per_launch": [{"offered": r["offered_pages_per_s"], "mode": r["mode"],
+                                   "steady_p99_us": p99(r), "one_per_launch_p99_us": p99(one[r["offered_pages_per_s"]]),
+                                   "beats_one_per_launch": p99(r) <= p99(one[r["offered_pages_per_s"]])}
+                                  for r in rows if r["mode"] != "one_per_launch"]}
     if rank == 0 and world == 1 and not args.no_cpu:
         threads = host_cores()
         v, npg, dt, passes = cpu_oracle_rate(args.cpu_seconds, threads)
@@ -533,6 +571,14 @@ def run_small(args):
 def run_batching(args):
     """20,000 Zipf(1.2) requests (1..512 pages, seed 3) scattered over an 8 GiB
     device buffer: one launch per request vs the persistent batched form."""
+    print(json.dumps(batching_result(args, args.batch_requests, args.feed_chunks)), flush=True)
+
+
+def batching_result(args, batch_requests, feed_chunks):
+    """The batching workload through one launch per request, graph-launched
+    batched submits (one row per entry of batch_requests) and the fed form
+    (one row per publication size in feed_chunks); every form's 8 GiB result
+    is compared with the one-launch-per-request buffer."""
     import numpy as np
     import torch
 
@@ -560,18 +606,22 @@ def run_batching(args):
     ptrs = [table_b.ctypes.data + 16 * int(o) for o in offsets[:-1]]
     szs = [int(x) for x in sizes]
     torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
+    ev0.record(stream)
     for r in range(n_req):
         rc = lib.ms_encrypt_pages(h, ptrs[r], szs[r])
         if rc:
             raise RuntimeError(ms.strerror(rc))
+    ev1.record(stream)
     if ctx.sync():
         raise RuntimeError("sync failed")
     t_single = time.perf_counter() - t0
+    span_single = ev0.elapsed_time(ev1)
 
     results = []
     applied = 0
-    for breq in args.batch_requests:
+    for breq in batch_requests:
         # a fixed number of requests per submit, or "rA-B": A requests first,
         # doubling on every submit up to B (the first kernel starts sooner, and
         # each fill still overlaps the previous submit's kernel)
@@ -603,15 +653,15 @@ def run_batching(args):
                         "gpu_span_ms": round(ev0.elapsed_time(ev1), 3), "identical_to_one_launch_per_request": ok})
     # the fed form: one persistent kernel drains the queue while the host is still filling it;
     # one untimed run first (the first run in a process pays one-time host costs)
-    if args.feed_chunks:
-        with ctx.feed(capacity=int(total), chunk=args.feed_chunks[0]) as fd:
+    if feed_chunks:
+        with ctx.feed(capacity=int(total), chunk=feed_chunks[0]) as fd:
             fd.open()
             fd.add_requests(ops, offsets, table_a)
             fd.close()
             if ctx.sync():
                 raise RuntimeError("sync failed")
         applied += 1
-    for chunk in args.feed_chunks:
+    for chunk in feed_chunks:
         with ctx.feed(capacity=int(total), chunk=chunk) as fd:   # allocation outside the timed span
             torch.cuda.synchronize()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -634,8 +684,11 @@ def run_batching(args):
                         "pages_per_s": round(total / el, 1), "gb_per_s": round(total * PAGE / el / 1e9, 2),
                         "gpu_span_ms": round(ev0.elapsed_time(ev1), 3), "identical_to_one_launch_per_request": ok})
     ctx.shutdown()
+    del a, b, plain
+    torch.cuda.empty_cache()
     best = max(results, key=lambda r: r["pages_per_s"])
-    print(json.dumps({
+    single = total / t_single
+    return {
         "metric": "batching pages/s (persistent kernel over a device work queue, autotuned: best of graph-launched "
                   "submits and the fed form)",
         "value": best["pages_per_s"], "unit": "pages/s", "higher_is_better": True, "best_form": best["requests_per_submit"],
@@ -644,35 +697,33 @@ def run_batching(args):
                                 f"({n_slots} slots), seed 3, ops 50/50 enc/dec"
                                 + ("" if args.batching_scale == 1.0 else " (profiling case)")),
                    "pages": total, "requests": n_req},
-        "one_launch_per_request": {"wall_s": round(t_single, 5), "pages_per_s": round(total / t_single, 1),
-                                   "gb_per_s": round(total * PAGE / t_single / 1e9, 2), "launches": n_req},
-        "speedup_vs_one_launch_per_request": round(best["pages_per_s"] / (total / t_single), 2),
+        "one_launch_per_request": {"wall_s": round(t_single, 5), "pages_per_s": round(single, 1),
+                                   "gb_per_s": round(total * PAGE / t_single / 1e9, 2), "launches": n_req,
+                                   "gpu_span_ms": round(span_single, 3)},
+        "speedup_vs_one_launch_per_request": round(best["pages_per_s"] / single, 2),
         "batched": results, "autotune": tune,
-    }), flush=True)
+    }
 
 
 # ---------------------------------------------------- host pages (config 4)
 def run_host(args):
     """4 GiB pinned host buffer (seed 4) streamed through the cipher in 2..64 MiB
     chunks on 2 streams; against the measured host-link bandwidth."""
+    print(json.dumps(host_result(args, args.chunks_mib)), flush=True)
+
+
+def host_link(hbuf, probe=1 << 30, reps=5):
+    """Pinned host-link rates (GB/s): host->device alone, device->host alone, and
+    each direction while both run at once (torch copies = cudaMemcpyAsync)."""
     import torch
-
-    import synth
-    from paper_2004_09252_b300 import memshield as ms
-
-    n = 1048576
-    key = synth.key_bytes(1)
-    hbuf = torch.empty(n * PAGE, dtype=torch.uint8).pin_memory()
-    synth.fill_pages(hbuf.data_ptr(), 4, 0, n)
-    head = hbuf[:PAGE * 64].clone()
-    # host-link probe: 1 GiB each way, pinned, cudaMemcpyAsync (torch copies)
-    probe = 1 << 30
+    probe = min(probe, hbuf.numel())
     dsrc = torch.empty(probe, dtype=torch.uint8, device="cuda")
     ddst = torch.empty(probe, dtype=torch.uint8, device="cuda")
     hin = hbuf[:probe]
     s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
 
-    def timed(fn, reps=5):
+    def timed(fn):
+        fn()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(reps):
@@ -689,14 +740,32 @@ def run_host(args):
             ddst.copy_(hin, non_blocking=True)
         with torch.cuda.stream(s2):
             scratch.copy_(dsrc, non_blocking=True)
-    bidir = timed(both)
-    bidir_each = probe / bidir / 1e9
+    bidir_each = probe / timed(both) / 1e9
     del dsrc, ddst, scratch
-    link_bound = min(bidir_each, h2d, d2h)
+    return {"h2d_gbs": round(h2d, 2), "d2h_gbs": round(d2h, 2), "bidirectional_each_gbs": round(bidir_each, 2),
+            "bound_gbs": round(min(bidir_each, h2d, d2h), 2),
+            "note": "the path moves every page both ways, so its bound is the slower direction while both run"}
+
+
+def host_result(args, chunks_mib):
+    """The host-page workload through ms_crypt_host at each chunk size, against
+    the measured host link."""
+    import torch
+
+    import synth
+    from paper_2004_09252_b300 import memshield as ms
+
+    n = 1048576
+    key = synth.key_bytes(1)
+    hbuf = torch.empty(n * PAGE, dtype=torch.uint8).pin_memory()
+    synth.fill_pages(hbuf.data_ptr(), 4, 0, n)
+    head = hbuf[:PAGE * 64].clone()
+    link = host_link(hbuf)
+    link_bound = link["bound_gbs"]
 
     ctx = ms.Context(key, stream=torch.cuda.current_stream())
     rows = []
-    for mib in args.chunks_mib:
+    for mib in chunks_mib:
         for ns in (2,) if mib != 16 else (2, 3, 4):
             ctx.crypt_host(ms.MS_ENCRYPT, hbuf, 0, n, mib << 20, ns)       # warm + leaves data encrypted
             torch.cuda.synchronize()
@@ -708,16 +777,14 @@ def run_host(args):
     ok = torch.equal(hbuf[:PAGE * 64], head)
     ctx.shutdown()
     best = max(rows, key=lambda r: r["gb_per_s"])
-    print(json.dumps({
+    return {
         "metric": "end-to-end host page GB/s (H2D + cipher + D2H)", "value": best["gb_per_s"], "unit": "GB/s",
         "higher_is_better": True,
         "config": {"workload": "host pages: 4 GiB pinned host buffer (1,048,576 pages, seed 4), ms_crypt_host, "
                                "chunks 2..64 MiB, 2..4 streams", "pages": n},
-        "link": {"h2d_gbs": round(h2d, 2), "d2h_gbs": round(d2h, 2), "bidirectional_each_gbs": round(bidir_each, 2),
-                 "bound_gbs": round(link_bound, 2)},
-        "frac_of_link": round(best["gb_per_s"] / link_bound, 3), "sweep": rows,
+        "link": link, "frac_of_link": round(best["gb_per_s"] / link_bound, 3), "sweep": rows,
         "round_trip_ok": ok,
-    }), flush=True)
+    }
 
 
 # ------------------------------------------------------- serving (config 5)
@@ -795,8 +862,27 @@ def resident_multi(args, ms, ctx, ws, n, rate, seconds):
     return lat, max(out[t][1] for t in range(T)), sum(int(loads[t][1][-1]) for t in range(T))
 
 
-def serve_rows(args, rates, modes, seconds):
-    """Replay the serving workload at each rate in each mode; one row per (rate, mode)."""
+def latency_split(arrival, lat):
+    """p50 / p99 / p99.9 (us) of the requests scheduled in the first second of a
+    run, and of the rest (the steady state; None when the run is shorter)."""
+    import numpy as np
+    us = lat * 1e6
+    out = {}
+    for name, sel in (("first_second", arrival < 1.0), ("steady", arrival >= 1.0)):
+        if not sel.any():
+            out[name] = None
+            continue
+        v = us[sel]
+        out[name] = {"requests": int(sel.sum()), "p50_us": round(float(np.percentile(v, 50)), 1),
+                     "p99_us": round(float(np.percentile(v, 99)), 1),
+                     "p999_us": round(float(np.percentile(v, 99.9)), 1)}
+    return out
+
+
+def serve_rows(args, rates, modes, seconds, one_per_launch_cap=None):
+    """Replay the serving workload at each rate in each mode; one row per (rate, mode).
+    Each run covers `seconds` of arrivals; one_per_launch_cap (requests) bounds
+    the one-launch-per-request runs, which saturate far below the top rates."""
     import numpy as np
     import torch
 
@@ -812,12 +898,21 @@ def serve_rows(args, rates, modes, seconds):
     ctx = ms.Context(key)
     ctx.autotune(65536)
     rows = []
+    mode_ids = {"continuous": ms.MS_SERVE_CONTINUOUS, "one_per_launch": ms.MS_SERVE_ONE_PER_LAUNCH,
+                "zero_copy": ms.MS_SERVE_ZERO_COPY}
     for rate in rates:
-        n_req = max(2000, int(rate / 8.0 * seconds))
-        arrival, ops, offsets, pages = synth.serving_workload(5, n_req, rate, n)
-        mode_ids = {"continuous": ms.MS_SERVE_CONTINUOUS, "one_per_launch": ms.MS_SERVE_ONE_PER_LAUNCH,
-                    "zero_copy": ms.MS_SERVE_ZERO_COPY}
+        n_full = max(2000, int(rate / 8.0 * seconds))
+        w_arrival, w_ops, w_offsets, w_pages = synth.serving_workload(5, n_full, rate, n)
+        warm = None
+        if args.serve_warmup_s > 0:   # a separate stream of requests (seed 55) at the same rate
+            warm = synth.serving_workload(55, max(200, int(rate / 8.0 * args.serve_warmup_s)), rate, n)
         for name in modes:
+            n_req = n_full
+            if name == "one_per_launch" and one_per_launch_cap:
+                n_req = min(n_req, one_per_launch_cap)
+            arrival, ops = w_arrival[:n_req], w_ops[:n_req]
+            offsets = w_offsets[:n_req + 1]
+            pages = w_pages[:int(offsets[-1])]
             reps = []
             for _ in range(max(1, args.serve_reps)):
                 if name == "resident" and args.resident_submitters > 1:
@@ -826,6 +921,8 @@ def serve_rows(args, rates, modes, seconds):
                           "gather_ns": 0, "scatter_ns": 0}
                 elif name == "resident":
                     with ms.Resident(ctx, workers=args.resident_workers) as res:
+                        if warm is not None:
+                            res.replay(ws, n, warm[0], warm[2], warm[3], timeout_ms=60000)
                         lat, makespan = res.replay(ws, n, arrival, offsets, pages, timeout_ms=60000)
                         rst = res.stats()
                     st = {"waves": rst["requests"], "max_wave_requests": 1, "conflict_waits": 0, "budget_waits": 0,
@@ -835,28 +932,39 @@ def serve_rows(args, rates, modes, seconds):
                                    waves_in_flight=args.waves_in_flight, idle_spin_us=args.idle_spin_us,
                                    max_wave_pages=args.max_wave_pages,
                                    zero_copy_max_pages=args.zero_copy_max_pages) as srv:
+                        if warm is not None:
+                            srv.replay(warm[0], warm[1], warm[2], warm[3], timeout_ms=600000)
+                        st0 = srv.stats()
                         lat, makespan = srv.replay(arrival, ops, offsets, pages, timeout_ms=600000)
                         st = srv.stats()
+                        for k in ("waves", "conflict_waits", "budget_waits", "gather_ns", "scatter_ns"):
+                            st[k] -= st0[k]
                 multi = name == "resident" and args.resident_submitters > 1
                 total = st["waves"] if multi else int(offsets[-1])
                 us = lat * 1e6
                 # p99 of the requests scheduled in each second of the run (single-submitter runs)
                 by_sec = []
+                split = None
                 if not multi:
                     sec = np.floor(arrival).astype(np.int64)
                     by_sec = [round(float(np.percentile(us[sec == k], 99)), 1) for k in range(int(sec.max()) + 1)
                               if (sec == k).any()]
+                    split = latency_split(arrival, lat)
                 reps.append({"sustained_pages_per_s": total / makespan, "p50_us": float(np.percentile(us, 50)),
                              "p99_us": float(np.percentile(us, 99)), "p999_us": float(np.percentile(us, 99.9)),
-                             "by_sec": by_sec, "st": st})
+                             "by_sec": by_sec, "split": split, "st": st})
             # medians over the repetitions (single-run tails are noisy on a shared host)
             med = {k: float(np.median([r[k] for r in reps])) for k in ("sustained_pages_per_s", "p50_us", "p99_us",
                                                                       "p999_us")}
-            st = reps[len(reps) // 2]["st"]
+            mid = reps[len(reps) // 2]
+            st = mid["st"]
             rows.append({"offered_pages_per_s": rate, "mode": name, "requests": n_req, "pages": total,
+                         "arrival_s": round(float(arrival[-1]), 2),
                          "sustained_pages_per_s": round(med["sustained_pages_per_s"], 1),
                          "p50_us": round(med["p50_us"], 1), "p99_us": round(med["p99_us"], 1),
                          "p999_us": round(med["p999_us"], 1), "reps": len(reps),
+                         "first_second": mid["split"]["first_second"] if mid["split"] else None,
+                         "steady": mid["split"]["steady"] if mid["split"] else None,
                          "p99_us_each": [round(r["p99_us"], 1) for r in reps],
                          "p99_us_by_second": [r["by_sec"] for r in reps],
                          "max_submit_lag_ms": [r["st"].get("submit_lag_ms") for r in reps],
@@ -1034,9 +1142,11 @@ def main():
     ap.add_argument("--shape", default="", help="K1 shape override: bpt,tpc,unroll,rot_policy[,hoist]")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-serving", action="store_true", help="skip the short serving summary in the bulk line")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving summary in the bulk line")
+    ap.add_argument("--no-batching", action="store_true", help="skip the batching summary in the bulk line")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--e2e-chunk-mib", type=int, default=16)
+    ap.add_argument("--e2e-pages", type=int, default=1048576, help="host-page e2e buffer (default 4 GiB)")
     ap.add_argument("--e2e-streams", type=int, default=2)
     ap.add_argument("--workload", choices=["bulk", "small", "batching", "host", "serving", "window", "pipes"],
                     default="bulk",
@@ -1044,6 +1154,11 @@ def main():
     ap.add_argument("--serve-pages", type=int, default=4194304, help="working-set pages (default 16 GiB)")
     ap.add_argument("--serve-rates", type=lambda v: [float(x) for x in v.split(",")], default=SERVE_RATES)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-warmup-s", type=float, default=0.0,
+                    help="serving: replay this many seconds of a separate request stream (seed 55) at the same "
+                         "rate, untimed, before each measured run")
+    ap.add_argument("--one-per-launch-cap", type=int, default=50000,
+                    help="serving: requests per one-launch-per-request run at most (it saturates near 270k pages/s)")
     ap.add_argument("--copy-threads", type=int, default=8)
     ap.add_argument("--serve-reps", type=int, default=1, help="repetitions per serving configuration (medians reported)")
     ap.add_argument("--resident-workers", type=int, default=8)

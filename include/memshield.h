@@ -417,8 +417,9 @@ int ms_tune_load(ms_ctx *ctx, const char *path);
  */
 typedef struct ms_server ms_server;
 
-/* Continuous mode stages large waves and runs small ones (zero_copy_max_pages)
- * in place; MS_SERVE_ONE_PER_LAUNCH always stages.
+/* Continuous mode stages its waves, except that with zero_copy_max_pages it
+ * runs small waves in place when the queue is short; MS_SERVE_ONE_PER_LAUNCH
+ * always stages.
  * MS_SERVE_ZERO_COPY: no staging copies; the kernel reads and writes the
  * working set directly over the host link (it must be pinned, mapped memory,
  * e.g. from cudaHostAlloc); the staging budget then only bounds the pages in
@@ -435,10 +436,12 @@ typedef struct ms_server_config {
   uint32_t zero_staging;     /* nonzero: wipe staging pages after each wave */
   uint32_t max_request_pages;/* largest request accepted (default 4096; <= staging pages) */
   uint32_t idle_spin_us;     /* idle server thread polls this long before sleeping (default 2000) */
-  uint32_t zero_copy_max_pages; /* continuous mode: a wave of at most this many pages skips staging and
-                                  runs in place on the working set when it is pinned, mapped memory
-                                  (default 0 = always staged; 16 lowers p50 by ~20 % but showed
-                                  sporadic multi-ms p99 at 141k pages/s) */
+  uint32_t zero_copy_max_pages; /* continuous mode, working set in pinned mapped memory: the in-place
+                                  lane.  While everything queued fits in this many pages (<= 512),
+                                  the wave runs in place on the working set -- one launch with the
+                                  entries in the kernel parameters, on its own stream, no staging
+                                  copies -- and completes independently of staged waves.  0 (the
+                                  default) = every wave staged */
 } ms_server_config;
 
 typedef struct ms_server_stats {
@@ -452,6 +455,7 @@ typedef struct ms_server_stats {
   uint64_t max_staged_pages; /* most staging slots ever in use (never above the budget) */
   uint64_t gather_ns;        /* server-thread time spent copying pages into staging */
   uint64_t scatter_ns;       /* ... and back into the working set */
+  uint64_t inplace_waves;    /* waves run through the in-place lane (included in waves) */
 } ms_server_stats;
 
 void ms_server_config_default(ms_server_config *cfg);

@@ -15,6 +15,12 @@
 //   - in one-per-launch mode a wave holds one request.
 // A wave that does not fit before the end of the ring starts at slot 0, and
 // the skipped tail counts as used until the wave is released.
+//
+// form_inplace(): a wave that takes no staging slots (it runs in place on the
+// working set), formed only while the whole queue holds at most max_pages
+// pages: every queued request whose pages are free joins it, in arrival
+// order, under the same blocking rule.  Its release frees no slots, so such
+// waves may be released in any order.
 #pragma once
 
 #include <algorithm>
@@ -103,8 +109,50 @@ class Admission {
     return true;
   }
 
+  // A wave for the in-place lane (see the top of the file): false when the
+  // queue holds more than max_pages pages or nothing can be admitted.
+  template <typename PagesOf>
+  bool form_inplace(std::deque<uint64_t> &queue, PagesOf pages_of, AdmittedWave &w, uint32_t max_pages) {
+    if (queue.empty() || queue.size() > max_pages) return false;
+    uint32_t total = 0;
+    for (uint64_t t : queue) total += (uint32_t)pages_of(t).size();
+    if (total > max_pages) return false;
+    std::vector<uint64_t> blocked, keep;
+    uint32_t len = 0;
+    for (uint64_t t : queue) {
+      const auto &pages = pages_of(t);
+      bool conflict = false;
+      for (uint64_t pg : pages)
+        if (busy_[pg]) {
+          conflict = true;
+          break;
+        }
+      if (conflict) {
+        ++conflict_waits;
+        for (uint64_t pg : pages)
+          if (!busy_[pg]) {
+            busy_[pg] = 2;
+            blocked.push_back(pg);
+          }
+        keep.push_back(t);
+        continue;
+      }
+      for (uint64_t pg : pages) busy_[pg] = 1;
+      len += (uint32_t)pages.size();
+      w.tickets.push_back(t);
+    }
+    for (uint64_t pg : blocked) busy_[pg] = 0;
+    if (w.tickets.empty()) return false;
+    queue.assign(keep.begin(), keep.end());
+    w.pos = 0;
+    w.len = len;
+    w.span = 0;
+    return true;
+  }
+
   // A completed wave: its pages leave the in-flight set and its slots are
-  // freed.  Waves must be released in the order form() returned them.
+  // freed.  Waves with slots must be released in the order form() returned
+  // them; in-place waves (span 0) in any order.
   template <typename PagesOf>
   void release(const AdmittedWave &w, PagesOf pages_of) {
     for (uint64_t t : w.tickets)

@@ -10,6 +10,15 @@
 // Staging is a ring of S page slots (pinned host) mirrored on the device,
 // with one 16-byte kernel entry per slot.  A wave occupies a contiguous run
 // of slots; waves are freed in issue order.
+//
+// In-place lane (continuous mode, working set in pinned mapped memory,
+// zero_copy_max_pages = N > 0): while everything queued fits in N pages, the
+// server forms the wave without staging slots and runs it in place on the
+// working set: one launch on a stream of its own with the entries in the
+// kernel's parameters -- no gather, no copies, no scatter.  Such waves
+// complete as soon as their kernel does, independently of the staged waves
+// (up to kInplaceDepth at once); under load the queue outgrows N and waves
+// are staged as before.
 #include <sys/prctl.h>
 #include <time.h>
 
@@ -147,6 +156,8 @@ struct Wave : ms::AdmittedWave {
   bool zc = false;  // run in place on the working set (no staging copies)
 };
 
+constexpr size_t kInplaceDepth = 4;  // in-place waves in flight at most
+
 }  // namespace
 
 struct ms_server {
@@ -158,6 +169,8 @@ struct ms_server {
   uint8_t *h_stage = nullptr, *d_stage = nullptr;
   ms_page_dom *h_ent = nullptr, *d_ent = nullptr;
   cudaStream_t s_in = nullptr, s_work[2] = {nullptr, nullptr};
+  cudaStream_t s_fast = nullptr;  // the in-place lane
+  uint32_t inplace_max = 0;       // pages of an in-place wave at most (0: lane off)
   std::vector<Req> reqs;
   std::mutex qmu;
   std::condition_variable qcv;
@@ -165,6 +178,7 @@ struct ms_server {
   std::atomic<uint64_t> next_ticket{0};
   ms::Admission *adm = nullptr;  // staging ring and in-flight pages (guarded by qmu)
   std::deque<Wave> inflight;
+  std::deque<Wave> inflight_inplace;  // completed in any order
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
   uint64_t wave_seq = 0;
   std::thread th;
@@ -175,14 +189,17 @@ struct ms_server {
   std::mutex done_mu;
   std::condition_variable done_cv;
   std::atomic<uint64_t> st_req{0}, st_pages{0}, st_waves{0}, st_maxreq{0}, st_maxpages{0}, st_conflict{0},
-      st_budget{0}, st_maxstaged{0}, st_gather_ns{0}, st_scatter_ns{0};
+      st_budget{0}, st_maxstaged{0}, st_gather_ns{0}, st_scatter_ns{0}, st_inplace{0};
   uint64_t d_host = 0;  // device address of host_base (zero-copy mode)
   uint64_t idle_spin_ns = 0;
 
   Req &slot(uint64_t t) { return reqs[t % reqs.size()]; }
   void loop();
   bool form_wave(Wave &w);
+  bool form_inplace(Wave &w);
   int issue(Wave &w);
+  int issue_inplace(Wave &w);
+  bool take_events(Wave &w);
   void complete(Wave &w);
   void fail_all(int code);
 };
@@ -210,19 +227,61 @@ bool ms_server::form_wave(Wave &w) {
   return ok;
 }
 
-int ms_server::issue(Wave &w) {
+bool ms_server::form_inplace(Wave &w) {
+  std::lock_guard<std::mutex> lk(qmu);
+  const bool ok = adm->form_inplace(incoming, [&](uint64_t t) -> const std::vector<uint64_t> & { return slot(t).pages; },
+                                    w, inplace_max);
+  st_conflict.store(adm->conflict_waits);
+  return ok;
+}
+
+bool ms_server::take_events(Wave &w) {
   if (ev_pool.empty()) {
     cudaEvent_t a, b;
-    if (cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess) return MS_ECUDA;
+    if (cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess) return false;
     if (cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
       cudaEventDestroy(a);
-      return MS_ECUDA;
+      return false;
     }
     ev_pool.push_back({a, b});
   }
   w.ev_h2d = ev_pool.back().first;
   w.ev_done = ev_pool.back().second;
   ev_pool.pop_back();
+  return true;
+}
+
+// An in-place wave: one launch with the entries in the kernel's parameters.
+int ms_server::issue_inplace(Wave &w) {
+  if (!take_events(w)) return cuda_fail(ctx, cudaGetLastError());
+  ms_page_dom ent[512];
+  uint32_t k = 0;
+  for (uint64_t t : w.tickets) {
+    Req &r = slot(t);
+    r.state.store(kAdmitted, std::memory_order_release);
+    for (uint64_t pg : r.pages) {
+      ent[k].addr = d_host + pg * MS_PAGE_BYTES;
+      ent[k].page_id = pg;
+      ent[k].domain = r.domain;
+      ent[k].reserved0 = 0;
+      ent[k].reserved1 = 0;
+      ++k;
+    }
+  }
+  w.zc = true;
+  cudaError_t e = injected(MS_FAULT_SERVER);
+  if (e == cudaSuccess) e = launch_pages_inline(ctx, ent, k, s_fast);
+  if (e == cudaSuccess) e = cudaEventRecord(w.ev_done, s_fast);
+  if (e != cudaSuccess) return cuda_fail(ctx, e);
+  st_waves.fetch_add(1);
+  st_inplace.fetch_add(1);
+  atomic_max(st_maxreq, w.tickets.size());
+  atomic_max(st_maxpages, w.len);
+  return MS_OK;
+}
+
+int ms_server::issue(Wave &w) {
+  if (!take_events(w)) return cuda_fail(ctx, cudaGetLastError());
   // slot index of every page of the wave, in order
   std::vector<std::pair<uint64_t, uint32_t>> map;  // (working-set page, staging slot)
   map.reserve(w.len);
@@ -235,9 +294,9 @@ int ms_server::issue(Wave &w) {
       map.push_back({pg, k++});
     }
   }
-  // zero-copy mode, or a small wave in continuous mode with a mapped working set
-  const bool zc = cfg.mode == MS_SERVE_ZERO_COPY || (d_host && cfg.mode == MS_SERVE_CONTINUOUS &&
-                                                     w.len <= cfg.zero_copy_max_pages);
+  // zero-copy mode: the kernel works on the working set itself (small waves
+  // of continuous mode go through the in-place lane instead, issue_inplace)
+  const bool zc = cfg.mode == MS_SERVE_ZERO_COPY;
   w.zc = zc;
   const uint64_t tg = now_ns();
   if (zc) {  // the kernel works on the working set itself, through the host link
@@ -326,11 +385,12 @@ void ms_server::complete(Wave &w) {
 void ms_server::fail_all(int code) {
   error.store(code);
   std::lock_guard<std::mutex> lk(qmu);
-  for (Wave &w : inflight)
-    for (uint64_t t : w.tickets) {
-      slot(t).error.store(code);
-      slot(t).state.store(kDone);
-    }
+  for (auto *set : {&inflight, &inflight_inplace})
+    for (Wave &w : *set)
+      for (uint64_t t : w.tickets) {
+        slot(t).error.store(code);
+        slot(t).state.store(kDone);
+      }
   for (uint64_t t : incoming) {
     slot(t).error.store(code);
     slot(t).state.store(kDone);
@@ -363,20 +423,51 @@ void ms_server::loop() {
       inflight.pop_front();
       progress = true;
     }
+    for (auto it = inflight_inplace.begin(); it != inflight_inplace.end();) {
+      cudaError_t q = cudaEventQuery(it->ev_done);
+      if (q == cudaErrorNotReady) {
+        ++it;
+        continue;
+      }
+      if (q != cudaSuccess) {
+        cuda_fail(ctx, q);
+        fail_all(MS_ECUDA);
+        exited.store(true);
+        return;
+      }
+      complete(*it);
+      it = inflight_inplace.erase(it);
+      progress = true;
+    }
     if (stop.load()) {
       bool empty;
       {
         std::lock_guard<std::mutex> lk(qmu);
         empty = incoming.empty();
       }
-      if (empty && inflight.empty()) break;
+      if (empty && inflight.empty() && inflight_inplace.empty()) break;
       if (!stop_deadline) stop_deadline = now_ns() + (uint64_t)ctx->cfg.timeout_ms * 1000000ull;
       if (now_ns() > stop_deadline) {
         fail_all(MS_ETIMEDOUT);
         break;
       }
     }
-    if (inflight.size() < cfg.waves_in_flight && error.load() == 0) {
+    bool formed = false;
+    if (inplace_max && inflight_inplace.size() < kInplaceDepth && error.load() == 0) {
+      Wave w;
+      if (form_inplace(w)) {
+        int rc = issue_inplace(w);
+        if (rc != MS_OK) {
+          inflight_inplace.push_back(w);
+          fail_all(rc);
+          exited.store(true);
+          return;
+        }
+        inflight_inplace.push_back(std::move(w));
+        progress = formed = true;
+      }
+    }
+    if (!formed && inflight.size() < cfg.waves_in_flight && error.load() == 0) {
       Wave w;
       if (form_wave(w)) {
         int rc = issue(w);
@@ -394,7 +485,7 @@ void ms_server::loop() {
       idle_since = 0;
       continue;
     }
-    if (inflight.empty()) {
+    if (inflight.empty() && inflight_inplace.empty()) {
       // idle: watch the ticket counter for a while before blocking, so a
       // request that arrives soon is picked up without a wake-up delay
       const uint64_t seen = next_ticket.load(), t_idle = now_ns();
@@ -425,7 +516,7 @@ void ms_server_config_default(ms_server_config *cfg) {
   cfg->mode = MS_SERVE_CONTINUOUS;
   cfg->max_request_pages = 4096;
   cfg->idle_spin_us = 2000;
-  cfg->zero_copy_max_pages = 0;  // in-place small waves: lower p50, but sporadic ms tails measured at 141k pages/s
+  cfg->zero_copy_max_pages = 0;  // the in-place lane is off unless asked for
 }
 
 static void free_server(ms_server *s) {
@@ -436,6 +527,7 @@ static void free_server(ms_server *s) {
     cudaEventDestroy(p.second);
   }
   if (s->s_in) cudaStreamDestroy(s->s_in);
+  if (s->s_fast) cudaStreamDestroy(s->s_fast);
   for (auto &w : s->s_work)
     if (w) cudaStreamDestroy(w);
   if (s->h_stage) cudaFreeHost(s->h_stage);
@@ -465,6 +557,7 @@ int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_serv
   if (cfg.max_wave_pages == 0) cfg.max_wave_pages = std::max<uint32_t>(1, S / cfg.waves_in_flight);
   if (cfg.max_request_pages == 0) cfg.max_request_pages = 4096;
   if (cfg.max_request_pages > S || cfg.max_request_pages > cfg.max_wave_pages) return MS_EINVAL;
+  if (cfg.zero_copy_max_pages > 512) return MS_EINVAL;  // an in-place wave's entries fit the kernel parameters
 
   ms_server *s = new (std::nothrow) ms_server();
   if (!s) return MS_ENOMEM;
@@ -486,6 +579,7 @@ int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_serv
       s->cfg.zero_copy_max_pages = 0;  // pageable working set: every wave is staged
     } else {
       s->d_host = (uint64_t)dp;
+      if (cfg.mode == MS_SERVE_CONTINUOUS) s->inplace_max = cfg.zero_copy_max_pages;
     }
   }
   cudaError_t e = cudaHostAlloc(&s->h_stage, (size_t)S * MS_PAGE_BYTES, cudaHostAllocDefault);
@@ -495,6 +589,11 @@ int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_serv
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_work[0], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_work[1], cudaStreamNonBlocking);
+  if (e == cudaSuccess && s->inplace_max) {
+    int lo = 0, hi = 0;  // the in-place lane's stream at the highest priority: a fault waits on it
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    e = cudaStreamCreateWithPriority(&s->s_fast, cudaStreamNonBlocking, hi);
+  }
   if (e != cudaSuccess) {
     free_server(s);
     return alloc_fail(c, e);
@@ -685,6 +784,7 @@ int ms_server_get_stats(const ms_server *s, ms_server_stats *out) {
   out->max_staged_pages = s->st_maxstaged.load();
   out->gather_ns = s->st_gather_ns.load();
   out->scatter_ns = s->st_scatter_ns.load();
+  out->inplace_waves = s->st_inplace.load();
   return MS_OK;
 }
 
@@ -697,12 +797,14 @@ int ms_server_destroy(ms_server *s) {
   DeviceGuard g(s->ctx->device);
   // everything the server issued must be finished before its buffers go:
   // the waves still listed, and any copy of a wave whose issue failed midway
-  for (Wave &w : s->inflight) {
-    if (!w.ev_done) continue;  // its issue failed before it had events
-    int r = wait_event(s->ctx, w.ev_done, s->ctx->cfg.timeout_ms);
-    if (r != MS_OK) return r;  // still running on the GPU: leave the buffers allocated
-  }
-  for (cudaStream_t st : {s->s_in, s->s_work[0], s->s_work[1]}) {
+  for (auto *set : {&s->inflight, &s->inflight_inplace})
+    for (Wave &w : *set) {
+      if (!w.ev_done) continue;  // its issue failed before it had events
+      int r = wait_event(s->ctx, w.ev_done, s->ctx->cfg.timeout_ms);
+      if (r != MS_OK) return r;  // still running on the GPU: leave the buffers allocated
+    }
+  for (cudaStream_t st : {s->s_in, s->s_work[0], s->s_work[1], s->s_fast}) {
+    if (!st) continue;
     cudaEvent_t ev;
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return cuda_fail(s->ctx, cudaGetLastError());
     cudaError_t e = cudaEventRecord(ev, st);
@@ -710,9 +812,11 @@ int ms_server_destroy(ms_server *s) {
     cudaEventDestroy(ev);
     if (r != MS_OK) return r;
   }
-  for (Wave &w : s->inflight)
-    if (w.ev_done) s->ev_pool.push_back({w.ev_h2d, w.ev_done});
+  for (auto *set : {&s->inflight, &s->inflight_inplace})
+    for (Wave &w : *set)
+      if (w.ev_done) s->ev_pool.push_back({w.ev_h2d, w.ev_done});
   s->inflight.clear();
+  s->inflight_inplace.clear();
   ms_ctx *c = s->ctx;
   free_server(s);
   c->children.fetch_sub(1);

@@ -6,7 +6,10 @@
 //   - a page is never in two in-flight waves, nor twice in one wave;
 //   - requests that share a page are admitted in arrival order;
 //   - every request is admitted in the end (no starvation).
-// Usage: admission_sim seed slots max_wave one_per_launch n_pages n_req max_req_pages depth
+// With inplace_max > 0, in-place waves (form_inplace: no staging slots, at
+// most inplace_max pages, formed only while the whole queue fits) are mixed
+// in and complete in random order; the same checks cover them.
+// Usage: admission_sim seed slots max_wave one_per_launch n_pages n_req max_req_pages depth inplace_max
 #include <cstdio>
 #include <cstdlib>
 #include <deque>
@@ -33,13 +36,14 @@ static uint64_t rnd() {  // splitmix64 step
   } while (0)
 
 int main(int argc, char **argv) {
-  if (argc != 9) return 2;
+  if (argc != 10) return 2;
   s_state = std::strtoull(argv[1], nullptr, 10);
   const uint32_t S = (uint32_t)std::atoi(argv[2]), max_wave = (uint32_t)std::atoi(argv[3]);
   const bool one = std::atoi(argv[4]) != 0;
   const uint64_t n_pages = std::strtoull(argv[5], nullptr, 10);
   const size_t n_req = std::strtoull(argv[6], nullptr, 10);
   const uint32_t max_req = (uint32_t)std::atoi(argv[7]), depth = (uint32_t)std::atoi(argv[8]);
+  const uint32_t inplace_max = (uint32_t)std::atoi(argv[9]);
 
   std::vector<std::vector<uint64_t>> pages(n_req);
   for (size_t r = 0; r < n_req; ++r) {
@@ -51,10 +55,10 @@ int main(int argc, char **argv) {
   ms::Admission adm(S, max_wave, one, n_pages, 64);
   auto pages_of = [&](uint64_t t) -> const std::vector<uint64_t> & { return pages[t]; };
   std::deque<uint64_t> queue;
-  std::deque<ms::AdmittedWave> inflight;
+  std::deque<ms::AdmittedWave> inflight, inplace;
   std::vector<long> admitted_at(n_req, -1);
   std::map<uint64_t, std::vector<uint64_t>> page_order;  // page -> tickets in admission order
-  size_t next = 0, done = 0;
+  size_t next = 0, done = 0, n_inplace = 0;
   long step = 0;
   while (done < n_req) {
     if (++step > 50000000) FAIL("no progress");
@@ -62,13 +66,17 @@ int main(int argc, char **argv) {
     if (x < 3 && next < n_req) {  // arrivals
       const size_t k = 1 + rnd() % 8;
       for (size_t i = 0; i < k && next < n_req; ++i) queue.push_back(next++);
-    } else if (x < 6 && inflight.size() < depth) {
+    } else if (x < 6 && (inflight.size() < depth || inplace.size() < depth)) {
       ms::AdmittedWave w;
-      if (adm.form(queue, pages_of, w)) {
-        if (w.pos + w.len > S || w.span < w.len) FAIL("wave outside the ring: pos %u len %u", w.pos, w.len);
+      bool ip = false, ok = false;
+      if (inplace_max && inplace.size() < depth) ok = ip = adm.form_inplace(queue, pages_of, w, inplace_max);
+      if (!ok && inflight.size() < depth) ok = adm.form(queue, pages_of, w);
+      if (ok) {
+        if (ip && (w.span != 0 || w.len > inplace_max)) FAIL("in-place wave: span %u len %u", w.span, w.len);
+        if (!ip && (w.pos + w.len > S || w.span < w.len)) FAIL("wave outside the ring: pos %u len %u", w.pos, w.len);
         if (adm.used() > S) FAIL("ring over-used: %u > %u", adm.used(), S);
-        if (one && w.tickets.size() != 1) FAIL("one-per-launch wave with %zu requests", w.tickets.size());
-        if (w.len > max_wave && w.tickets.size() > 1) FAIL("wave of %u pages", w.len);
+        if (!ip && one && w.tickets.size() != 1) FAIL("one-per-launch wave with %zu requests", w.tickets.size());
+        if (!ip && w.len > max_wave && w.tickets.size() > 1) FAIL("wave of %u pages", w.len);
         uint32_t len = 0;
         std::set<uint64_t> in_wave;
         for (uint64_t t : w.tickets) {
@@ -80,16 +88,23 @@ int main(int argc, char **argv) {
           }
         }
         if (len != w.len) FAIL("wave length %u, requests hold %u pages", w.len, len);
-        for (const auto &o : inflight) {
-          const bool overlap = !(w.pos + w.len <= o.pos || o.pos + o.len <= w.pos);
-          if (overlap) FAIL("slots [%u,%u) overlap in-flight [%u,%u)", w.pos, w.pos + w.len, o.pos, o.pos + o.len);
-          for (uint64_t t : o.tickets)
-            for (uint64_t pg : pages[t])
-              if (in_wave.count(pg)) FAIL("page %llu in two in-flight waves", (unsigned long long)pg);
-        }
-        inflight.push_back(w);
+        for (const auto *set : {&inflight, &inplace})
+          for (const auto &o : *set) {
+            const bool overlap = !ip && o.span && !(w.pos + w.len <= o.pos || o.pos + o.len <= w.pos);
+            if (overlap) FAIL("slots [%u,%u) overlap in-flight [%u,%u)", w.pos, w.pos + w.len, o.pos, o.pos + o.len);
+            for (uint64_t t : o.tickets)
+              for (uint64_t pg : pages[t])
+                if (in_wave.count(pg)) FAIL("page %llu in two in-flight waves", (unsigned long long)pg);
+          }
+        (ip ? inplace : inflight).push_back(w);
+        n_inplace += ip;
       }
-    } else if (!inflight.empty()) {  // the oldest wave completes
+    } else if (!inplace.empty() && (inflight.empty() || rnd() % 2)) {  // any in-place wave completes
+      const size_t i = rnd() % inplace.size();
+      adm.release(inplace[i], pages_of);
+      done += inplace[i].tickets.size();
+      inplace.erase(inplace.begin() + (long)i);
+    } else if (!inflight.empty()) {  // the oldest staged wave completes
       adm.release(inflight.front(), pages_of);
       done += inflight.front().tickets.size();
       inflight.pop_front();
@@ -103,7 +118,8 @@ int main(int argc, char **argv) {
         FAIL("page %llu: request %llu admitted before earlier request %llu", (unsigned long long)kv.first,
              (unsigned long long)kv.second[i], (unsigned long long)kv.second[i - 1]);
   if (adm.used() != 0) FAIL("ring not empty at the end: %u", adm.used());
-  std::printf("OK requests %zu conflict_waits %llu budget_waits %llu\n", n_req,
-              (unsigned long long)adm.conflict_waits, (unsigned long long)adm.budget_waits);
+  if (inplace_max && n_inplace == 0) FAIL("no in-place wave was formed");
+  std::printf("OK requests %zu conflict_waits %llu budget_waits %llu in_place_waves %zu\n", n_req,
+              (unsigned long long)adm.conflict_waits, (unsigned long long)adm.budget_waits, n_inplace);
   return 0;
 }

@@ -20,13 +20,17 @@ def sim(tmp_path_factory):
 
 
 CASES = [
-    # seed, slots, max_wave, one_per_launch, n_pages, n_req, max_req_pages, depth
-    (1, 64, 32, 0, 200, 3000, 8, 2),       # small ring, frequent wrap, many conflicts
-    (2, 64, 32, 0, 40, 3000, 8, 4),        # tiny page space: conflicts everywhere
-    (3, 100, 50, 0, 1000, 5000, 50, 3),    # requests as large as the wave
-    (4, 128, 64, 1, 300, 3000, 16, 2),     # one request per wave
-    (5, 4096, 2048, 0, 100000, 20000, 64, 2),
-    (6, 37, 37, 0, 50, 2000, 37, 8),       # odd ring size, requests filling the ring
+    # seed, slots, max_wave, one_per_launch, n_pages, n_req, max_req_pages, depth, inplace_max
+    (1, 64, 32, 0, 200, 3000, 8, 2, 0),       # small ring, frequent wrap, many conflicts
+    (2, 64, 32, 0, 40, 3000, 8, 4, 0),        # tiny page space: conflicts everywhere
+    (3, 100, 50, 0, 1000, 5000, 50, 3, 0),    # requests as large as the wave
+    (4, 128, 64, 1, 300, 3000, 16, 2, 0),     # one request per wave
+    (5, 4096, 2048, 0, 100000, 20000, 64, 2, 0),
+    (6, 37, 37, 0, 50, 2000, 37, 8, 0),       # odd ring size, requests filling the ring
+    (7, 64, 32, 0, 200, 3000, 4, 4, 32),      # in-place waves mixed in, completing in any order
+    (8, 64, 32, 0, 40, 3000, 3, 4, 24),       # ... with conflicts everywhere
+    (9, 4096, 2048, 0, 100000, 20000, 64, 2, 64),
+    (10, 256, 128, 0, 2000, 5000, 8, 3, 48),
 ]
 
 

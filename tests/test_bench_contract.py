@@ -25,7 +25,8 @@ def run_bench(*args, timeout=600):
 
 
 def test_default_line_keys():
-    d = run_bench("--steps", "4", "--warmup", "3", "--pages", "65536", "--no-serving", "--cpu-seconds", "1")
+    d = run_bench("--steps", "4", "--warmup", "3", "--pages", "65536", "--no-serving", "--no-batching",
+                  "--e2e-pages", "65536", "--cpu-seconds", "1")
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
               "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e", "clocks",
               "gpu_launches"):
@@ -39,9 +40,31 @@ def test_default_line_keys():
     e = d["e2e"]
     assert e["unit"] == "GB/s" and e["value"] > 0 and e["round_trip_ok"] is True
     assert e["h2d_bytes_per_step"] == e["d2h_bytes_per_step"] == 2 * 65536 * 4096
+    assert e["link"]["bound_gbs"] > 0 and 0 < e["frac_of_link"]
     c = d["cpu_baseline"]
     assert c["kind"] == "oracle" and c["cores"] >= 1 and c["value"] > 0 and c["sample"]
     assert set(d["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
+    assert d["clocks"]["samples"] >= 20 and d["clocks"]["sm_mhz"] > 0
+
+
+def test_default_line_batching_and_serving_summaries():
+    """The default line's batching and serving summaries, on a reduced batching
+    workload and a small working set (keys only)."""
+    d = run_bench("--steps", "3", "--warmup", "3", "--pages", "65536", "--no-e2e", "--no-cpu", "--batching-scale",
+                  "0.05", "--serve-pages", "65536", "--serve-seconds", "1.5", "--serve-rates", "10000,141000",
+                  "--one-per-launch-cap", "5000", timeout=900)
+    b = d["batching"]
+    assert b["unit"] == "pages/s" and b["fed"]["identical_to_one_launch_per_request"] is True
+    assert b["graph_launched"]["identical_to_one_launch_per_request"] is True
+    assert b["one_launch_per_request"]["pages_per_s"] > 0 and b["speedup_vs_one_launch_per_request"] > 0
+    rows = d["serving"]["rows"]
+    assert {(r["offered_pages_per_s"], r["mode"]) for r in rows} == {
+        (rate, m) for rate in (1e4, 1.41e5) for m in ("continuous", "one_per_launch", "resident")}
+    for r in rows:
+        assert r["first_second"]["p99_us"] > 0 and r["p99_us_by_second"]
+        if r["mode"] == "one_per_launch":
+            assert r["requests"] <= 5000
+    assert len(d["serving"]["vs_one_per_launch"]) == 4
 
 
 def test_reference_arm_line():
@@ -49,6 +72,7 @@ def test_reference_arm_line():
     assert d["impl"] == "reference" and d["unit"] == "GB/s" and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert f" {d['config']['pages']} pages" in d["cpu_baseline"]["sample"]    # the pages actually timed
 
 
 def test_small_workload_line():

@@ -58,13 +58,14 @@ def test_submit_wait_matches_oracle(ms, key1):
     assert st["requests_done"] == len(reqs) and st["pages_done"] == len(touched)
 
 
-@pytest.mark.parametrize("mode,zc_pages", [(0, None), (0, 16), (0, 4096), (1, None), (2, None)])
-def test_alone_equals_mix(ms, key1, mode, zc_pages):
+@pytest.mark.parametrize("mode,zc_pages,rate", [(0, None, 2e6), (0, 16, 2e6), (0, 16, 3e4), (0, 512, 2e5),
+                                                (1, None, 2e6), (2, None, 2e6)])
+def test_alone_equals_mix(ms, key1, mode, zc_pages, rate):
     """Each request's result is identical when served alone (submit, wait, one
-    at a time) and when served in a fast open-loop mix (bit-exact), and both
-    equal the oracle."""
+    at a time) and when served in an open-loop mix (bit-exact), and both equal
+    the oracle; at the lower rates the in-place lane carries waves."""
     n, n_req = 16384, 1500
-    arrival, ops, offsets, pages = distinct_workload(71, n_req, n, 2e6)
+    arrival, ops, offsets, pages = distinct_workload(71, n_req, n, rate)
     plain = synth.page_bytes_fast(72, 0, n)
     alone = torch.from_numpy(plain.copy()).pin_memory()
     mix = torch.from_numpy(plain.copy()).pin_memory()
@@ -87,6 +88,10 @@ def test_alone_equals_mix(ms, key1, mode, zc_pages):
         assert st["gather_ns"] < st["waves"] * 10**6      # no staging copies in zero-copy mode
     else:
         assert st["waves"] <= n_req
+    if zc_pages and rate < 1e6:
+        assert 0 < st["inplace_waves"] <= st["waves"]
+    elif not zc_pages:
+        assert st["inplace_waves"] == 0
 
 
 def test_conflicting_requests_serialise(ms, key1):
@@ -110,6 +115,42 @@ def test_conflicting_requests_serialise(ms, key1):
     odd = np.nonzero(counts % 2)[0].astype(np.uint64)
     assert np.array_equal(h.numpy(), oracle_ws(key1, plain, odd))
     assert st["conflict_waits"] > 0
+
+
+def test_in_place_lane_with_conflicts(ms, key1):
+    """Requests submitted a few at a time on overlapping pages, with the
+    in-place lane on: short queues go in place, longer ones are staged, and a
+    request on a page still in flight in either lane waits for it.  The final
+    state is the closed form of the application counts."""
+    n = 512
+    h = working_set(76, n)
+    plain = h.numpy().copy()
+    rng = synth.splitmix64(77, 0, 20000)
+    counts = np.zeros(n, dtype=np.int64)
+    with ms.Context(key1) as ctx, ms.Server(ctx, h, n, zero_copy_max_pages=16) as srv:
+        pending = []
+        for r in range(600):
+            x = int(rng[r] % np.uint64(64))
+            # every fifth request is 20 pages (always staged), the others one page
+            sel = (x + np.arange(20)) % 64 if r % 5 == 0 else np.array([x])
+            counts[sel] += 1
+            pending.append(srv.submit(r % 2, sel))
+            if r % 3 == 2:                 # let the queue drain now and then
+                srv.wait(pending.pop(0))
+        for t in pending:
+            srv.wait(t)
+        st = srv.stats()
+    odd = np.nonzero(counts % 2)[0].astype(np.uint64)
+    assert np.array_equal(h.numpy(), oracle_ws(key1, plain, odd))
+    assert st["inplace_waves"] > 0 and st["waves"] > st["inplace_waves"]
+
+
+def test_in_place_lane_limit(ms, key1):
+    h = working_set(78, 64)
+    with ms.Context(key1) as ctx:
+        with pytest.raises(ms.MemShieldError) as e:
+            ms.Server(ctx, h, 64, zero_copy_max_pages=513)
+        assert e.value.code == ms.MS_EINVAL
 
 
 def test_small_staging_budget(ms, key1):
