@@ -1,7 +1,8 @@
 // Sliding-window client driver: produces the paper's fault / eviction stream
 // (Sec. 4.3) from page-access traces and serves it through an ms_server
-// (staged waves) or through resident workers (one page per request, in place
-// on the pinned working set, as the paper's GPU module does).
+// (staged waves), through resident workers (one page per request, in place
+// on the pinned working set, as the paper's GPU module does) or through
+// ticketed launches on per-client clones of a context.
 //
 // Each client owns a range of working-set pages, all encrypted at the start,
 // and a FIFO window of pages in clear.  An access to a page outside the
@@ -13,18 +14,10 @@
 // waits for its encryption through the server's in-flight rule).  Clients
 // run on their own threads with their own domain (the paper's PID).
 //
-// Background eviction (the paper's conclusions propose starting to encrypt
-// window pages in the background once the free slots drop below a
-// threshold): with background_free = T > 0 every client also gets an
-// evictor thread.  Whenever fewer than T of the window's slots are free, the
-// evictor encrypts the oldest clear pages until T are free again, so the
-// faulting thread only decrypts.  The client and its evictor share the
-// window under one lock, and every request that touches a page is submitted
-// under that lock, so each backend sees a page's eviction before any later
-// fault on it (the server's in-flight rule, a resident wait on the eviction's
-// ticket, or the clone's stream order then keep them apart on the GPU).  A
-// faulting page joins the window only once its decryption has completed,
-// so the evictor never picks a page whose fault is still running.
+// With background_free = T > 0 each client also runs an evictor thread that
+// keeps T window slots free (the paper's conclusions propose encrypting window
+// pages in the background).  The client and evictor logic is in
+// ms_window_client.h; this file supplies the three backends.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
