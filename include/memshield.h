@@ -514,10 +514,11 @@ int ms_server_get_stats(const ms_server *srv, ms_server_stats *out);
  * window pages in the background once the number of free slots drops below
  * a threshold): with background_free = T (1 .. window_pages - 1) each client
  * also runs an evictor thread.  Whenever fewer than T of the window's
- * window_pages slots are free, the evictor encrypts the oldest clear pages
- * (requests of at most evict_batch pages) until T slots are free again, off
- * the faulting thread's path; the overflow rule above stays as the fallback
- * when the evictor runs behind.  Client and evictor share the window under
+ * window_pages slots are free, the evictor encrypts the oldest evict_batch
+ * clear pages by one request, again until at least T slots are free, off the
+ * faulting thread's path (a batch larger than the shortfall evicts ahead of
+ * need); the overflow rule above stays as the fallback when the evictor runs
+ * behind.  Client and evictor share the window under
  * one lock; a page's eviction is always submitted before any later fault on
  * it, and a faulting page joins the window only once it is decrypted.
  * Each client runs on its own thread; its requests use its domain (PID).

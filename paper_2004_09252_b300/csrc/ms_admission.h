@@ -47,12 +47,14 @@ class Admission {
   uint64_t conflict_waits = 0, budget_waits = 0;
 
   // pages_of(ticket) returns the request's page list (a container of uint64_t).
+  // The cost is proportional to the requests scanned, not to the queue: a
+  // one-request wave taken from a long backlog touches only the head.
   template <typename PagesOf>
   bool form(std::deque<uint64_t> &queue, PagesOf pages_of, AdmittedWave &w) {
     if (used_ == 0) head_ = 0;  // nothing in flight: the whole ring is free from slot 0
     uint32_t pos = head_, waste = 0, len = 0;
     const size_t window = std::min(queue.size(), window_);
-    std::vector<uint8_t> taken(window, 0);
+    std::vector<uint8_t> taken;  // one flag per scanned request
     std::vector<uint64_t> blocked;
     size_t n_taken = 0;
     for (size_t i = 0; i < window; ++i) {
@@ -82,6 +84,7 @@ class Admission {
             busy_[pg] = 2;  // blocked for the rest of this scan
             blocked.push_back(pg);
           }
+        taken.push_back(0);
         continue;
       }
       for (uint64_t pg : pages) busy_[pg] = 1;
@@ -89,17 +92,18 @@ class Admission {
       waste = wst;
       len += n;
       w.tickets.push_back(queue[i]);
-      taken[i] = 1;
+      taken.push_back(1);
       ++n_taken;
     }
     for (uint64_t pg : blocked) busy_[pg] = 0;
     if (n_taken == 0) return false;
-    // drop the admitted tickets from the scanned prefix, keeping the others in order
+    // drop the admitted tickets from the scanned prefix, keeping the skipped ones in order
+    const size_t scanned = taken.size();
     std::vector<uint64_t> keep;
-    keep.reserve(window - n_taken);
-    for (size_t i = 0; i < window; ++i)
+    keep.reserve(scanned - n_taken);
+    for (size_t i = 0; i < scanned; ++i)
       if (!taken[i]) keep.push_back(queue[i]);
-    queue.erase(queue.begin(), queue.begin() + (long)window);
+    queue.erase(queue.begin(), queue.begin() + (long)scanned);
     for (size_t i = keep.size(); i-- > 0;) queue.push_front(keep[i]);
     w.pos = pos;
     w.len = len;

@@ -68,7 +68,9 @@ int evict_oldest(Backend &be, Window &w, uint32_t domain, size_t k, ClientRun &c
 }
 
 // The background evictor: whenever fewer than T slots are free, encrypt the
-// oldest pages (requests of at most evict_batch) until T are free again.
+// oldest evict_batch pages in one request, again until at least T are free.
+// A batch larger than the shortfall evicts ahead of need: one wake-up and
+// one request serve evict_batch faults.
 template <typename Backend>
 void run_evictor(Backend &be, const ms_window_config &cfg, Window &w, uint32_t domain, ClientRun &cr) {
   const size_t keep = cfg.window_pages - cfg.background_free;  // pages the window may hold at rest
@@ -76,7 +78,7 @@ void run_evictor(Backend &be, const ms_window_config &cfg, Window &w, uint32_t d
   for (;;) {
     w.cv.wait(lk, [&] { return w.done || w.rc != MS_OK || w.pages.size() > keep; });
     while (w.rc == MS_OK && w.pages.size() > keep) {
-      const size_t k = std::min<size_t>(cfg.evict_batch, w.pages.size() - keep);
+      const size_t k = std::min<size_t>(cfg.evict_batch, w.pages.size());
       const int rc = evict_oldest(be, w, domain, k, cr, true);
       if (rc != MS_OK) w.rc = rc;
     }
