@@ -45,6 +45,7 @@ using ms::window::run_client;
 struct ServerBackend {
   ms_server *srv;
   uint32_t timeout_ms;
+  std::mutex emu;  // evict_tickets: the client and its evictor both evict
   std::vector<uint64_t> evict_tickets;
   int fault_submit(uint32_t domain, uint64_t pg, uint64_t *ticket) {
     // an eviction of this page still in flight is waited for by the server's in-flight rule
@@ -63,7 +64,10 @@ struct ServerBackend {
       if (rc != MS_EBUSY) break;
       std::this_thread::yield();
     }
-    if (rc == MS_OK) evict_tickets.push_back(ticket);
+    if (rc == MS_OK) {
+      std::lock_guard<std::mutex> lk(emu);
+      evict_tickets.push_back(ticket);
+    }
     return rc;
   }
   int drain() {
@@ -80,7 +84,11 @@ struct ResidentBackend {
   uint64_t dbase;       // device address of the working set
   uint64_t first_page;  // the client's range, for last_ticket
   uint32_t timeout_ms;
-  std::vector<uint64_t> last_ticket;  // per client page: its latest request, ~0 = none
+  // per client page: its latest eviction, ~0 = none.  An element is written by
+  // the thread that evicts the page and read by a later fault on it, which
+  // the window's order puts after that eviction's submission.
+  std::vector<uint64_t> last_ticket;
+  std::mutex emu;  // evict_tickets: the client and its evictor both evict
   std::vector<uint64_t> evict_tickets;
   int submit(uint32_t domain, uint64_t pg, uint64_t *ticket) {
     ms_page_dom e{};
@@ -111,6 +119,7 @@ struct ResidentBackend {
       const int rc = submit(domain, pages[i], &ticket);
       if (rc != MS_OK) return rc;
       last_ticket[pages[i] - first_page] = ticket;
+      std::lock_guard<std::mutex> lk(emu);
       evict_tickets.push_back(ticket);
     }
     return MS_OK;
@@ -131,10 +140,10 @@ struct TicketBackend {
   ms_ctx *ctx;
   uint64_t dbase;
   uint32_t timeout_ms;
+  std::mutex emu;                // last_evict: the client and its evictor both evict
   uint64_t last_evict = ~0ull;  // the client's latest eviction ticket
-  std::vector<ms_page> ent;
   int submit(const uint64_t *pages, size_t k, uint64_t *ticket, int op) {
-    ent.resize(k);
+    std::vector<ms_page> ent(k);
     for (size_t i = 0; i < k; ++i) {
       ent[i].addr = dbase + pages[i] * MS_PAGE_BYTES;
       ent[i].page_id = pages[i];
@@ -152,7 +161,10 @@ struct TicketBackend {
   int evict(uint32_t, const uint64_t *pages, size_t k) {
     uint64_t t;
     const int rc = submit(pages, k, &t, MS_ENCRYPT);
-    if (rc == MS_OK) last_evict = t;
+    if (rc == MS_OK) {  // tickets of one context grow with submission order
+      std::lock_guard<std::mutex> lk(emu);
+      if (last_evict == ~0ull || t > last_evict) last_evict = t;
+    }
     return rc;
   }
   int drain() { return last_evict == ~0ull ? MS_OK : ms_wait(ctx, last_evict, timeout_ms); }
@@ -216,7 +228,7 @@ extern "C" int ms_window_run(ms_server *srv, const ms_window_config *cfg, const 
   const int rc = check_window_args(cfg, clients, n_clients, ~0ull);
   if (rc != MS_OK) return rc;
   return run_clients(*cfg, clients, n_clients, stats_out, final_window_out, [&](const ms_window_client &) {
-    return ServerBackend{srv, timeout_ms, {}};
+    return ServerBackend{srv, timeout_ms, {}, {}};
   });
 }
 
@@ -233,9 +245,8 @@ extern "C" int ms_window_run_resident(ms_resident *res, void *host_base, uint64_
     return MS_EINVAL;  // the working set must be pinned, mapped memory
   }
   return run_clients(*cfg, clients, n_clients, stats_out, final_window_out, [&](const ms_window_client &cl) {
-    ResidentBackend be{res, (uint64_t)dbase, cl.first_page, timeout_ms, {}, {}};
-    be.last_ticket.assign(cl.n_pages, ~0ull);
-    return be;
+    return ResidentBackend{res, (uint64_t)dbase, cl.first_page, timeout_ms,
+                           std::vector<uint64_t>(cl.n_pages, ~0ull), {}, {}};
   });
 }
 
@@ -252,7 +263,7 @@ extern "C" int ms_window_run_ticketed(ms_ctx *ctx, void *host_base, uint64_t n_p
   for (size_t c = 0; c < n_clients && rc == MS_OK; ++c) rc = ms_clone(ctx, clients[c].domain, &clones[c]);
   if (rc == MS_OK) {
     rc = run_clients(*cfg, clients, n_clients, stats_out, final_window_out, [&](const ms_window_client &cl) {
-      return TicketBackend{clones[(size_t)(&cl - clients)], dbase, timeout_ms, ~0ull, {}};
+      return TicketBackend{clones[(size_t)(&cl - clients)], dbase, timeout_ms, {}, ~0ull};
     });
   }
   for (ms_ctx *k : clones)

@@ -8,12 +8,15 @@
 //   fault_wait(ticket)                   wait for it
 //   evict(domain, pages, k)              queue an encrypt of k pages (not waited for)
 //   drain()                              wait for every eviction queued
-// fault_submit and evict are only called under the client's window lock, so
-// the order in which they reach the backend is the order of the window's
-// changes; the backend must apply a page's requests in that order.
+// A page's requests reach the backend in the order of the window's changes
+// (fault_submit under the client's window lock; an eviction before any later
+// fault on its pages), and the backend must apply them in that order.  The
+// background evictor calls evict from its own thread, concurrently with the
+// client's calls: a backend's calls must be safe to make from two threads.
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdint>
@@ -40,47 +43,74 @@ struct ClientRun {
   int rc = MS_OK;
 };
 
-// The window a client shares with its evictor (all fields under mu).
+// The window a client shares with its evictor.  Every field but `size` and
+// `evictor_asleep` is guarded by mu.
 struct Window {
   std::mutex mu;
-  std::condition_variable cv;  // wakes the evictor
-  std::deque<uint64_t> pages;  // working-set page indices in clear, oldest first
+  std::condition_variable wake;       // wakes an evictor that has gone to sleep
+  std::condition_variable submitted;  // an eviction taken out of the window reached the backend
+  std::deque<uint64_t> pages;         // working-set page indices in clear, oldest first
   std::unordered_set<uint64_t> members;
-  bool done = false;           // the client has finished its trace
-  int rc = MS_OK;              // the first error of either thread
+  std::vector<uint64_t> evicting;     // taken out by the evictor, eviction not yet submitted
+  std::atomic<size_t> size{0};        // pages.size(), read by the evictor without mu
+  std::atomic<bool> evictor_asleep{false};
+  bool done = false;                  // the client has finished its trace
+  int rc = MS_OK;                     // the first error of either thread
 };
 
-// Encrypt the oldest k pages of the window (one request); caller holds w.mu.
-template <typename Backend>
-int evict_oldest(Backend &be, Window &w, uint32_t domain, size_t k, ClientRun &cr, bool background) {
+// Take the oldest k pages out of the window; caller holds w.mu.
+inline std::vector<uint64_t> take_oldest(Window &w, size_t k) {
   std::vector<uint64_t> ev(w.pages.begin(), w.pages.begin() + (long)k);
   w.pages.erase(w.pages.begin(), w.pages.begin() + (long)k);
   for (uint64_t e : ev) w.members.erase(e);
-  const int rc = be.evict(domain, ev.data(), k);
-  if (rc != MS_OK) return rc;
+  w.size.store(w.pages.size(), std::memory_order_relaxed);
+  return ev;
+}
+
+inline void count_eviction(ClientRun &cr, size_t k, bool background) {
   cr.st.evictions += k;
   cr.st.evict_requests += 1;
   if (background) {
     cr.st.background_evictions += k;
     cr.st.background_requests += 1;
   }
-  return MS_OK;
 }
 
-// The background evictor: whenever fewer than T slots are free, encrypt the
-// oldest evict_batch pages in one request, again until at least T are free.
-// A batch larger than the shortfall evicts ahead of need: one wake-up and
-// one request serve evict_batch faults.
+// The background evictor: whenever fewer than T slots are free, take the
+// oldest evict_batch pages out of the window and encrypt them by one request,
+// again until at least T slots are free.  A batch larger than the shortfall
+// evicts ahead of need.  The pages leave the window under the lock but the
+// request is submitted outside it, so the client keeps faulting meanwhile; a
+// fault on one of those very pages waits until its eviction is submitted
+// (Window::evicting), which keeps the per-page order.  Between triggers the
+// evictor polls the window's size for a while before it sleeps, so that the
+// client rarely pays for a wake-up.
 template <typename Backend>
 void run_evictor(Backend &be, const ms_window_config &cfg, Window &w, uint32_t domain, ClientRun &cr) {
   const size_t keep = cfg.window_pages - cfg.background_free;  // pages the window may hold at rest
-  std::unique_lock<std::mutex> lk(w.mu);
   for (;;) {
-    w.cv.wait(lk, [&] { return w.done || w.rc != MS_OK || w.pages.size() > keep; });
+    const auto spin_end = clk::now() + std::chrono::microseconds(200);
+    while (w.size.load(std::memory_order_relaxed) <= keep && clk::now() < spin_end) std::this_thread::yield();
+    std::unique_lock<std::mutex> lk(w.mu);
+    if (w.pages.size() <= keep && !w.done && w.rc == MS_OK) {
+      w.evictor_asleep.store(true);
+      w.wake.wait(lk, [&] { return w.done || w.rc != MS_OK || w.pages.size() > keep; });
+      w.evictor_asleep.store(false);
+    }
     while (w.rc == MS_OK && w.pages.size() > keep) {
       const size_t k = std::min<size_t>(cfg.evict_batch, w.pages.size());
-      const int rc = evict_oldest(be, w, domain, k, cr, true);
-      if (rc != MS_OK) w.rc = rc;
+      std::vector<uint64_t> ev = take_oldest(w, k);
+      w.evicting.insert(w.evicting.end(), ev.begin(), ev.end());
+      lk.unlock();
+      const int rc = be.evict(domain, ev.data(), k);
+      lk.lock();
+      for (uint64_t e : ev) w.evicting.erase(std::find(w.evicting.begin(), w.evicting.end(), e));
+      w.submitted.notify_all();
+      if (rc != MS_OK) {
+        w.rc = rc;
+        break;
+      }
+      count_eviction(cr, k, true);
     }
     if (w.done || w.rc != MS_OK) return;
   }
@@ -107,7 +137,7 @@ void run_client(Backend &be, const ms_window_config &cfg, ClientRun &cr) {
     uint64_t ticket = 0;
     std::chrono::steady_clock::time_point f0;
     {
-      std::lock_guard<std::mutex> lk(w.mu);
+      std::unique_lock<std::mutex> lk(w.mu);
       if (w.rc != MS_OK) {
         rc = w.rc;
         break;
@@ -117,9 +147,13 @@ void run_client(Backend &be, const ms_window_config &cfg, ClientRun &cr) {
         cr.st.hits += 1;
         continue;
       }
-      // fault: the decrypt is submitted under the lock, after any eviction of this page
       f0 = clk::now();
-      rc = be.fault_submit(cl.domain, pg, &ticket);
+      // fault: a page the evictor has just taken out is decrypted only after
+      // its eviction is submitted, and the decrypt is submitted under the lock
+      w.submitted.wait(lk, [&] {
+        return w.rc != MS_OK || std::find(w.evicting.begin(), w.evicting.end(), pg) == w.evicting.end();
+      });
+      rc = w.rc != MS_OK ? w.rc : be.fault_submit(cl.domain, pg, &ticket);
     }
     if (rc == MS_OK) rc = be.fault_wait(ticket);  // the faulting thread is stalled until it is resolved
     if (rc != MS_OK) break;
@@ -128,11 +162,15 @@ void run_client(Backend &be, const ms_window_config &cfg, ClientRun &cr) {
     cr.st.faults += 1;
     w.pages.push_back(pg);
     w.members.insert(pg);
+    w.size.store(w.pages.size(), std::memory_order_relaxed);
     if (w.pages.size() > cfg.window_pages) {  // overflow (without an evictor, or one running behind)
-      rc = evict_oldest(be, w, cl.domain, std::min<size_t>(cfg.evict_batch, w.pages.size()), cr, false);
+      const size_t k = std::min<size_t>(cfg.evict_batch, w.pages.size());
+      std::vector<uint64_t> ev = take_oldest(w, k);
+      rc = be.evict(cl.domain, ev.data(), k);
       if (rc != MS_OK) break;
+      count_eviction(cr, k, false);
     }
-    if (bg && w.pages.size() > keep) w.cv.notify_one();
+    if (bg && w.pages.size() > keep && w.evictor_asleep.load()) w.wake.notify_one();
   }
   if (bg) {
     {
@@ -140,7 +178,7 @@ void run_client(Backend &be, const ms_window_config &cfg, ClientRun &cr) {
       w.done = true;
       if (rc != MS_OK && w.rc == MS_OK) w.rc = rc;
     }
-    w.cv.notify_one();
+    w.wake.notify_one();
     evictor.join();  // it brings the window back to T free slots before it leaves
     if (rc == MS_OK) rc = w.rc;
   }

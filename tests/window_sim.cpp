@@ -137,6 +137,7 @@ class FakeGpu {
 
 struct FakeBackend {
   FakeGpu *g;
+  std::mutex emu;  // the client and its evictor both evict
   std::vector<uint64_t> evicts;
   int fault_submit(uint32_t, uint64_t pg, uint64_t *ticket) {
     *ticket = g->submit(MS_DECRYPT, &pg, 1);
@@ -144,7 +145,9 @@ struct FakeBackend {
   }
   int fault_wait(uint64_t t) { return g->wait(t); }
   int evict(uint32_t, const uint64_t *pages, size_t k) {
-    evicts.push_back(g->submit(MS_ENCRYPT, pages, k));
+    const uint64_t t = g->submit(MS_ENCRYPT, pages, k);
+    std::lock_guard<std::mutex> lk(emu);
+    evicts.push_back(t);
     return MS_OK;
   }
   int drain() {
@@ -194,7 +197,7 @@ int main(int argc, char **argv) {
   for (int c = 0; c < n_clients; ++c) {
     runs[c].cl = &clients[c];
     th.emplace_back([&, c] {
-      FakeBackend be{&gpu, {}};
+      FakeBackend be{&gpu, {}, {}};
       ms::window::run_client(be, cfg, runs[c]);
     });
   }
