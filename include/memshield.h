@@ -417,8 +417,8 @@ int ms_tune_load(ms_ctx *ctx, const char *path);
  */
 typedef struct ms_server ms_server;
 
-/* Continuous mode stages its waves, except that with zero_copy_max_pages it
- * runs small waves in place when the queue is short; MS_SERVE_ONE_PER_LAUNCH
+/* Continuous mode stages its waves, except that (zero_copy_max_pages) it runs
+ * small waves in place when the queue is short; MS_SERVE_ONE_PER_LAUNCH
  * always stages.
  * MS_SERVE_ZERO_COPY: no staging copies; the kernel reads and writes the
  * working set directly over the host link (it must be pinned, mapped memory,
@@ -435,13 +435,14 @@ typedef struct ms_server_config {
   uint32_t mode;             /* ms_serve_mode */
   uint32_t zero_staging;     /* nonzero: wipe staging pages after each wave */
   uint32_t max_request_pages;/* largest request accepted (default 4096; <= staging pages) */
-  uint32_t idle_spin_us;     /* idle server thread polls this long before sleeping (default 2000) */
+  uint32_t idle_spin_us;     /* idle server thread polls this long before sleeping (default 20000:
+                                a trickle of faults does not find it asleep) */
   uint32_t zero_copy_max_pages; /* continuous mode, working set in pinned mapped memory: the in-place
                                   lane.  While everything queued fits in this many pages (<= 512),
                                   the wave runs in place on the working set -- one launch with the
                                   entries in the kernel parameters, on its own stream, no staging
-                                  copies -- and completes independently of staged waves.  0 (the
-                                  default) = every wave staged */
+                                  copies -- and completes independently of staged waves.  Default
+                                  64 (any one request of the serving mix); 0 = every wave staged */
 } ms_server_config;
 
 typedef struct ms_server_stats {

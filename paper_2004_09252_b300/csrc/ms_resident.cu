@@ -246,6 +246,7 @@ int ensure_running(ms_resident *r, int wi) {
   Worker &w = *r->w[wi];
   __atomic_thread_fence(__ATOMIC_SEQ_CST);
   uint32_t st = load_acq32(&w.h_sh->state);
+  if (st == kRunning) return MS_OK;  // the common case: no clock read
   const auto limit = std::chrono::steady_clock::now() + std::chrono::milliseconds(r->ctx->cfg.timeout_ms);
   while (st == kExiting) {  // the worker is deciding; it resolves within a few microseconds
     if (std::chrono::steady_clock::now() > limit) return MS_ETIMEDOUT;
@@ -541,6 +542,9 @@ extern "C" int ms_resident_replay(ms_resident *r, void *host_base, uint64_t n_pa
       if (target - t > 200000) nap_ns((long)(target - t - 100000));
     }
     sched[q] = target;
+    if (q + 1 < n)  // the next request's entries of the page-sized ticket table: hide their cache misses
+      for (uint64_t k = offsets[q + 1]; k < offsets[q + 2] && k < offsets[q + 1] + 16; ++k)
+        __builtin_prefetch(&last_ticket[page_index[k]]);
     for (uint64_t k = offsets[q]; k < offsets[q + 1] && rc == MS_OK; ++k) {
       const uint64_t pg = page_index[k];
       if (last_ticket[pg] != ~0ull) {

@@ -515,8 +515,8 @@ void ms_server_config_default(ms_server_config *cfg) {
   cfg->max_pending = 1u << 18;
   cfg->mode = MS_SERVE_CONTINUOUS;
   cfg->max_request_pages = 4096;
-  cfg->idle_spin_us = 2000;
-  cfg->zero_copy_max_pages = 0;  // the in-place lane is off unless asked for
+  cfg->idle_spin_us = 20000;
+  cfg->zero_copy_max_pages = 64;  // the in-place lane takes any one request of the serving mix
 }
 
 static void free_server(ms_server *s) {
