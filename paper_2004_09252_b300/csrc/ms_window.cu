@@ -56,7 +56,7 @@ struct ServerBackend {
     }
   }
   int fault_wait(uint64_t ticket) { return ms_server_wait(srv, ticket, timeout_ms); }
-  int evict(uint32_t domain, const uint64_t *pages, size_t k) {
+  int evict(uint32_t domain, const uint64_t *pages, size_t k, bool) {
     uint64_t ticket;
     int rc;
     for (;;) {
@@ -113,7 +113,7 @@ struct ResidentBackend {
     return submit(domain, pg, ticket);
   }
   int fault_wait(uint64_t ticket) { return ms_resident_wait(res, ticket, timeout_ms); }
-  int evict(uint32_t domain, const uint64_t *pages, size_t k) {
+  int evict(uint32_t domain, const uint64_t *pages, size_t k, bool) {
     for (size_t i = 0; i < k; ++i) {
       uint64_t ticket;
       const int rc = submit(domain, pages[i], &ticket);
@@ -134,15 +134,26 @@ struct ResidentBackend {
 };
 
 // One launch per request on a context, each with its own ticket (in place on
-// the pinned working set).  The context's stream runs requests in submission
-// order, so a fault on a page whose eviction is still queued runs after it.
+// the pinned working set).  The client's context runs its requests in
+// submission order, so a fault on a page whose eviction it queued earlier
+// runs after it.  The background evictor submits on a second clone (its own
+// lock and stream), so its launches neither hold up the client's calls nor
+// queue ahead of its faults; a fault on a page whose background eviction is
+// still pending waits for that eviction's ticket first.
 struct TicketBackend {
-  ms_ctx *ctx;
+  ms_ctx *ctx;      // the client's faults and its own evictions
+  ms_ctx *bg_ctx;   // the evictor's evictions (nullptr without background eviction)
   uint64_t dbase;
+  uint64_t first_page;
   uint32_t timeout_ms;
-  std::mutex emu;                // last_evict: the client and its evictor both evict
-  uint64_t last_evict = ~0ull;  // the client's latest eviction ticket
-  int submit(const uint64_t *pages, size_t k, uint64_t *ticket, int op) {
+  // per client page: its latest background eviction on bg_ctx, ~0 = none.  An
+  // element is written by the evictor and read by a later fault on the page,
+  // which the window's order puts after that eviction's submission.
+  std::vector<uint64_t> bg_ticket;
+  std::mutex emu;                  // the two latest eviction tickets
+  uint64_t last_evict = ~0ull, last_bg_evict = ~0ull;
+  static int submit(ms_ctx *c, uint64_t dbase, uint32_t timeout_ms, const uint64_t *pages, size_t k,
+                    uint64_t *ticket, int op) {
     std::vector<ms_page> ent(k);
     for (size_t i = 0; i < k; ++i) {
       ent[i].addr = dbase + pages[i] * MS_PAGE_BYTES;
@@ -150,24 +161,41 @@ struct TicketBackend {
     }
     const auto limit = clk::now() + std::chrono::milliseconds(timeout_ms);
     for (;;) {
-      const int rc = ms_submit_host(ctx, op, ent.data(), k, ticket);
+      const int rc = ms_submit_host(c, op, ent.data(), k, ticket);
       if (rc != MS_EBUSY) return rc;
       if (clk::now() > limit) return MS_ETIMEDOUT;
       std::this_thread::yield();
     }
   }
-  int fault_submit(uint32_t, uint64_t pg, uint64_t *ticket) { return submit(&pg, 1, ticket, MS_DECRYPT); }
-  int fault_wait(uint64_t ticket) { return ms_wait(ctx, ticket, timeout_ms); }
-  int evict(uint32_t, const uint64_t *pages, size_t k) {
-    uint64_t t;
-    const int rc = submit(pages, k, &t, MS_ENCRYPT);
-    if (rc == MS_OK) {  // tickets of one context grow with submission order
-      std::lock_guard<std::mutex> lk(emu);
-      if (last_evict == ~0ull || t > last_evict) last_evict = t;
+  int fault_submit(uint32_t, uint64_t pg, uint64_t *ticket) {
+    if (bg_ctx) {
+      uint64_t &t = bg_ticket[pg - first_page];
+      if (t != ~0ull) {  // its background eviction may still be pending on the other stream
+        const int rc = ms_wait(bg_ctx, t, timeout_ms);
+        if (rc != MS_OK) return rc;
+        t = ~0ull;
+      }
     }
+    return submit(ctx, dbase, timeout_ms, &pg, 1, ticket, MS_DECRYPT);
+  }
+  int fault_wait(uint64_t ticket) { return ms_wait(ctx, ticket, timeout_ms); }
+  int evict(uint32_t, const uint64_t *pages, size_t k, bool background) {
+    ms_ctx *c = background && bg_ctx ? bg_ctx : ctx;
+    uint64_t t;
+    const int rc = submit(c, dbase, timeout_ms, pages, k, &t, MS_ENCRYPT);
+    if (rc != MS_OK) return rc;
+    if (c == bg_ctx)
+      for (size_t i = 0; i < k; ++i) bg_ticket[pages[i] - first_page] = t;
+    std::lock_guard<std::mutex> lk(emu);  // tickets of one context grow with submission order
+    uint64_t &last = c == bg_ctx ? last_bg_evict : last_evict;
+    if (last == ~0ull || t > last) last = t;
+    return MS_OK;
+  }
+  int drain() {
+    int rc = last_evict == ~0ull ? MS_OK : ms_wait(ctx, last_evict, timeout_ms);
+    if (rc == MS_OK && last_bg_evict != ~0ull) rc = ms_wait(bg_ctx, last_bg_evict, timeout_ms);
     return rc;
   }
-  int drain() { return last_evict == ~0ull ? MS_OK : ms_wait(ctx, last_evict, timeout_ms); }
 };
 
 int check_window_args(const ms_window_config *cfg, const ms_window_client *clients, size_t n_clients,
@@ -258,15 +286,23 @@ extern "C" int ms_window_run_ticketed(ms_ctx *ctx, void *host_base, uint64_t n_p
   if (rc != MS_OK) return rc;
   uint64_t dbase = 0;
   if (ms_host_device_address(host_base, &dbase) != MS_OK) return MS_EINVAL;
-  // one clone per client: its PID as the domain, its own stream
-  std::vector<ms_ctx *> clones(n_clients, nullptr);
-  for (size_t c = 0; c < n_clients && rc == MS_OK; ++c) rc = ms_clone(ctx, clients[c].domain, &clones[c]);
+  // one clone per client: its PID as the domain, its own stream; with
+  // background eviction a second one for the client's evictor
+  const bool bg = cfg->background_free != 0;
+  std::vector<ms_ctx *> clones(n_clients, nullptr), bg_clones(n_clients, nullptr);
+  for (size_t c = 0; c < n_clients && rc == MS_OK; ++c) {
+    rc = ms_clone(ctx, clients[c].domain, &clones[c]);
+    if (rc == MS_OK && bg) rc = ms_clone(ctx, clients[c].domain, &bg_clones[c]);
+  }
   if (rc == MS_OK) {
     rc = run_clients(*cfg, clients, n_clients, stats_out, final_window_out, [&](const ms_window_client &cl) {
-      return TicketBackend{clones[(size_t)(&cl - clients)], dbase, timeout_ms, {}, ~0ull};
+      const size_t c = (size_t)(&cl - clients);
+      return TicketBackend{clones[c], bg_clones[c], dbase, cl.first_page, timeout_ms,
+                           std::vector<uint64_t>(bg ? cl.n_pages : 0, ~0ull), {}, ~0ull, ~0ull};
     });
   }
-  for (ms_ctx *k : clones)
-    if (k) ms_shutdown(k);
+  for (auto *set : {&clones, &bg_clones})
+    for (ms_ctx *k : *set)
+      if (k) ms_shutdown(k);
   return rc;
 }

@@ -6,7 +6,8 @@
 // A Backend provides, all returning MS_OK or an MS_E* code:
 //   fault_submit(domain, page, &ticket)  queue a one-page decrypt
 //   fault_wait(ticket)                   wait for it
-//   evict(domain, pages, k)              queue an encrypt of k pages (not waited for)
+//   evict(domain, pages, k, background)  queue an encrypt of k pages (not waited for);
+//                                        background: called by the evictor thread
 //   drain()                              wait for every eviction queued
 // A page's requests reach the backend in the order of the window's changes
 // (fault_submit under the client's window lock; an eviction before any later
@@ -102,7 +103,7 @@ void run_evictor(Backend &be, const ms_window_config &cfg, Window &w, uint32_t d
       std::vector<uint64_t> ev = take_oldest(w, k);
       w.evicting.insert(w.evicting.end(), ev.begin(), ev.end());
       lk.unlock();
-      const int rc = be.evict(domain, ev.data(), k);
+      const int rc = be.evict(domain, ev.data(), k, true);
       lk.lock();
       for (uint64_t e : ev) w.evicting.erase(std::find(w.evicting.begin(), w.evicting.end(), e));
       w.submitted.notify_all();
@@ -166,7 +167,7 @@ void run_client(Backend &be, const ms_window_config &cfg, ClientRun &cr) {
     if (w.pages.size() > cfg.window_pages) {  // overflow (without an evictor, or one running behind)
       const size_t k = std::min<size_t>(cfg.evict_batch, w.pages.size());
       std::vector<uint64_t> ev = take_oldest(w, k);
-      rc = be.evict(cl.domain, ev.data(), k);
+      rc = be.evict(cl.domain, ev.data(), k, false);
       if (rc != MS_OK) break;
       count_eviction(cr, k, false);
     }

@@ -144,7 +144,7 @@ struct FakeBackend {
     return MS_OK;
   }
   int fault_wait(uint64_t t) { return g->wait(t); }
-  int evict(uint32_t, const uint64_t *pages, size_t k) {
+  int evict(uint32_t, const uint64_t *pages, size_t k, bool) {
     const uint64_t t = g->submit(MS_ENCRYPT, pages, k);
     std::lock_guard<std::mutex> lk(emu);
     evicts.push_back(t);
