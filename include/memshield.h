@@ -438,7 +438,8 @@ typedef struct ms_server_config {
   uint32_t idle_spin_us;     /* idle server thread polls this long before sleeping (default 20000:
                                 a trickle of faults does not find it asleep) */
   uint32_t zero_copy_max_pages; /* continuous mode, working set in pinned mapped memory: the in-place
-                                  lane.  While everything queued fits in this many pages (<= 512),
+                                  lane.  While everything queued fits in this many pages (<= 512;
+                                  also capped by max_wave_pages),
                                   the wave runs in place on the working set -- one launch with the
                                   entries in the kernel parameters, on its own stream, no staging
                                   copies -- and completes independently of staged waves.  Default

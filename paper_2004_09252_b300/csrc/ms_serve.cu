@@ -579,7 +579,7 @@ int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_serv
       s->cfg.zero_copy_max_pages = 0;  // pageable working set: every wave is staged
     } else {
       s->d_host = (uint64_t)dp;
-      if (cfg.mode == MS_SERVE_CONTINUOUS) s->inplace_max = cfg.zero_copy_max_pages;
+      if (cfg.mode == MS_SERVE_CONTINUOUS) s->inplace_max = std::min(cfg.zero_copy_max_pages, cfg.max_wave_pages);
     }
   }
   cudaError_t e = cudaHostAlloc(&s->h_stage, (size_t)S * MS_PAGE_BYTES, cudaHostAllocDefault);
