@@ -980,9 +980,10 @@ def serve_rows(args, rates, modes, seconds, one_per_launch_cap=None):
 # ------------------------------------------- sliding-window clients (NEXT)
 def run_window(args):
     """Clients fault through FIFO windows of clear pages (Sec. 4.3), as in the
-    paper's Table 1 (window 4..32 pages) and Table 2 (1, 2, 4 instances), with
-    background eviction off (0) and on (the free-slot thresholds of
-    --window-free, the paper's proposed improvement)."""
+    paper's Table 1 (window 4..32 pages) and Table 2 (1, 2, 4 instances), under
+    three eviction policies: the paper's (each eviction finished before the
+    next fault), asynchronous evictions, and background eviction (the paper's
+    proposed improvement)."""
     import numpy as np
     import torch
 
@@ -1010,7 +1011,10 @@ def run_window(args):
             for n_cl in args.window_clients:
                 for wnd in args.window_sizes:
                     for batch in args.window_batches:
-                        for free in args.window_free:
+                        for policy in args.window_policies:
+                            # sync: the client waits for its own evictions (the paper's server);
+                            # async: it does not; background: an evictor keeps window_free slots free
+                            free = args.window_free if policy == "background" else 0
                             if batch > wnd + 1 or free >= wnd:
                                 continue
                             # clients resume from where the previous run left their windows: re-encrypt them first
@@ -1020,20 +1024,18 @@ def run_window(args):
                             state = {}
                             cl = [(1000 + c, c * per, per, traces[c]) for c in range(n_cl)]
                             t0 = time.perf_counter()
+                            kw = dict(timeout_ms=20000, background_free=free, sync_evict=policy == "sync")
                             if backend == "ticketed":   # one clone of ctx per client: its PID, its stream
-                                st, wins = ctx.run_window_clients(ws, n, wnd, batch, cl, timeout_ms=20000,
-                                                                  background_free=free)
+                                st, wins = ctx.run_window_clients(ws, n, wnd, batch, cl, **kw)
                             elif backend == "resident":
-                                st, wins = res.run_window_clients(ws, n, wnd, batch, cl, timeout_ms=20000,
-                                                                  background_free=free)
+                                st, wins = res.run_window_clients(ws, n, wnd, batch, cl, **kw)
                             else:
-                                st, wins = srv.run_window_clients(wnd, batch, cl, timeout_ms=20000,
-                                                                  background_free=free)
+                                st, wins = srv.run_window_clients(wnd, batch, cl, **kw)
                             el = time.perf_counter() - t0
                             state = {c: wins[c] for c in range(n_cl)}
                             faults = sum(x["faults"] for x in st)
                             rows.append({"backend": backend, "clients": n_cl, "window_pages": wnd,
-                                         "evict_batch": batch, "background_free": free,
+                                         "evict_batch": batch, "policy": policy, "background_free": free,
                                          "accesses": sum(x["accesses"] for x in st), "faults": faults,
                                          "evictions": sum(x["evictions"] for x in st),
                                          "evict_requests": sum(x["evict_requests"] for x in st),
@@ -1154,7 +1156,7 @@ def main():
     ap.add_argument("--serve-pages", type=int, default=4194304, help="working-set pages (default 16 GiB)")
     ap.add_argument("--serve-rates", type=lambda v: [float(x) for x in v.split(",")], default=SERVE_RATES)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
-    ap.add_argument("--serve-warmup-s", type=float, default=0.0,
+    ap.add_argument("--serve-warmup-s", type=float, default=0.3,
                     help="serving: replay this many seconds of a separate request stream (seed 55) at the same "
                          "rate, untimed, before each measured run")
     ap.add_argument("--one-per-launch-cap", type=int, default=50000,
@@ -1171,8 +1173,11 @@ def main():
     ap.add_argument("--window-clients", type=lambda v: [int(x) for x in v.split(",")], default=[1, 2, 4])
     ap.add_argument("--window-sizes", type=lambda v: [int(x) for x in v.split(",")], default=[4, 8, 16, 32])
     ap.add_argument("--window-batches", type=lambda v: [int(x) for x in v.split(",")], default=[1, 8])
-    ap.add_argument("--window-free", type=lambda v: [int(x) for x in v.split(",")], default=[0, 1],
-                    help="background eviction thresholds: free window slots the evictor keeps (0 = off)")
+    ap.add_argument("--window-policies", type=lambda v: v.split(","), default=["sync", "async", "background"],
+                    help="eviction policies: sync (the client waits for its evictions, as the paper's server), "
+                         "async (it does not), background (an evictor keeps --window-free slots free)")
+    ap.add_argument("--window-free", type=int, default=1,
+                    help="background eviction threshold: free window slots the evictor keeps")
     ap.add_argument("--window-backends", type=lambda v: v.split(","), default=["server", "resident", "ticketed"],
                     help="serve the window clients through the staged server, resident workers and/or "
                          "ticketed launches")

@@ -531,7 +531,10 @@ typedef struct ms_window_config {
   uint32_t window_pages;     /* maximum pages in clear per client (Table 1: 4, 8, 16, 32) */
   uint32_t evict_batch;      /* pages encrypted per eviction request, 1..window_pages + 1 */
   uint32_t background_free;  /* 0: no background eviction; else T, 1..window_pages - 1 (above) */
-  uint32_t reserved;         /* must be 0 */
+  uint32_t sync_evict;       /* nonzero: the client waits for each of its own overflow evictions
+                                before its next access, as the paper's per-client server thread
+                                finishes an eviction before it takes the next fault; 0: evictions
+                                are not waited for */
 } ms_window_config;
 
 typedef struct ms_window_client {

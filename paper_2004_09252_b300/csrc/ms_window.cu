@@ -47,6 +47,7 @@ struct ServerBackend {
   uint32_t timeout_ms;
   std::mutex emu;  // evict_tickets: the client and its evictor both evict
   std::vector<uint64_t> evict_tickets;
+  uint64_t last_own = ~0ull;  // the client's latest own eviction (written and read by the client)
   int fault_submit(uint32_t domain, uint64_t pg, uint64_t *ticket) {
     // an eviction of this page still in flight is waited for by the server's in-flight rule
     for (;;) {
@@ -56,7 +57,7 @@ struct ServerBackend {
     }
   }
   int fault_wait(uint64_t ticket) { return ms_server_wait(srv, ticket, timeout_ms); }
-  int evict(uint32_t domain, const uint64_t *pages, size_t k, bool) {
+  int evict(uint32_t domain, const uint64_t *pages, size_t k, bool background) {
     uint64_t ticket;
     int rc;
     for (;;) {
@@ -67,9 +68,11 @@ struct ServerBackend {
     if (rc == MS_OK) {
       std::lock_guard<std::mutex> lk(emu);
       evict_tickets.push_back(ticket);
+      if (!background) last_own = ticket;
     }
     return rc;
   }
+  int wait_evicted() { return last_own == ~0ull ? MS_OK : ms_server_wait(srv, last_own, timeout_ms); }
   int drain() {
     for (uint64_t t : evict_tickets) {
       const int rc = ms_server_wait(srv, t, timeout_ms);
@@ -90,6 +93,7 @@ struct ResidentBackend {
   std::vector<uint64_t> last_ticket;
   std::mutex emu;  // evict_tickets: the client and its evictor both evict
   std::vector<uint64_t> evict_tickets;
+  std::vector<uint64_t> own;  // the client's latest own eviction, one ticket per page (client only)
   int submit(uint32_t domain, uint64_t pg, uint64_t *ticket) {
     ms_page_dom e{};
     e.addr = dbase + pg * MS_PAGE_BYTES;
@@ -113,14 +117,23 @@ struct ResidentBackend {
     return submit(domain, pg, ticket);
   }
   int fault_wait(uint64_t ticket) { return ms_resident_wait(res, ticket, timeout_ms); }
-  int evict(uint32_t domain, const uint64_t *pages, size_t k, bool) {
+  int evict(uint32_t domain, const uint64_t *pages, size_t k, bool background) {
+    if (!background) own.clear();
     for (size_t i = 0; i < k; ++i) {
       uint64_t ticket;
       const int rc = submit(domain, pages[i], &ticket);
       if (rc != MS_OK) return rc;
       last_ticket[pages[i] - first_page] = ticket;
+      if (!background) own.push_back(ticket);
       std::lock_guard<std::mutex> lk(emu);
       evict_tickets.push_back(ticket);
+    }
+    return MS_OK;
+  }
+  int wait_evicted() {
+    for (uint64_t t : own) {
+      const int rc = ms_resident_wait(res, t, timeout_ms);
+      if (rc != MS_OK) return rc;
     }
     return MS_OK;
   }
@@ -152,6 +165,7 @@ struct TicketBackend {
   std::vector<uint64_t> bg_ticket;
   std::mutex emu;                  // the two latest eviction tickets
   uint64_t last_evict = ~0ull, last_bg_evict = ~0ull;
+  uint64_t last_own = ~0ull;       // the client's latest own eviction (on ctx)
   static int submit(ms_ctx *c, uint64_t dbase, uint32_t timeout_ms, const uint64_t *pages, size_t k,
                     uint64_t *ticket, int op) {
     std::vector<ms_page> ent(k);
@@ -189,8 +203,10 @@ struct TicketBackend {
     std::lock_guard<std::mutex> lk(emu);  // tickets of one context grow with submission order
     uint64_t &last = c == bg_ctx ? last_bg_evict : last_evict;
     if (last == ~0ull || t > last) last = t;
+    if (!background) last_own = t;
     return MS_OK;
   }
+  int wait_evicted() { return last_own == ~0ull ? MS_OK : ms_wait(ctx, last_own, timeout_ms); }
   int drain() {
     int rc = last_evict == ~0ull ? MS_OK : ms_wait(ctx, last_evict, timeout_ms);
     if (rc == MS_OK && last_bg_evict != ~0ull) rc = ms_wait(bg_ctx, last_bg_evict, timeout_ms);
@@ -202,7 +218,7 @@ int check_window_args(const ms_window_config *cfg, const ms_window_client *clien
                       uint64_t n_pages) {
   if (!cfg || (n_clients && !clients)) return MS_EINVAL;
   if (cfg->window_pages == 0 || cfg->evict_batch == 0 || cfg->evict_batch > cfg->window_pages + 1) return MS_EINVAL;
-  if (cfg->background_free >= cfg->window_pages || cfg->reserved) return MS_EINVAL;
+  if (cfg->background_free >= cfg->window_pages) return MS_EINVAL;
   for (size_t c = 0; c < n_clients; ++c) {
     if (!clients[c].trace && clients[c].trace_len) return MS_EINVAL;
     if (clients[c].first_page > n_pages || clients[c].n_pages > n_pages - clients[c].first_page) return MS_EINVAL;
@@ -274,7 +290,7 @@ extern "C" int ms_window_run_resident(ms_resident *res, void *host_base, uint64_
   }
   return run_clients(*cfg, clients, n_clients, stats_out, final_window_out, [&](const ms_window_client &cl) {
     return ResidentBackend{res, (uint64_t)dbase, cl.first_page, timeout_ms,
-                           std::vector<uint64_t>(cl.n_pages, ~0ull), {}, {}};
+                           std::vector<uint64_t>(cl.n_pages, ~0ull), {}, {}, {}};
   });
 }
 
@@ -298,7 +314,7 @@ extern "C" int ms_window_run_ticketed(ms_ctx *ctx, void *host_base, uint64_t n_p
     rc = run_clients(*cfg, clients, n_clients, stats_out, final_window_out, [&](const ms_window_client &cl) {
       const size_t c = (size_t)(&cl - clients);
       return TicketBackend{clones[c], bg_clones[c], dbase, cl.first_page, timeout_ms,
-                           std::vector<uint64_t>(bg ? cl.n_pages : 0, ~0ull), {}, ~0ull, ~0ull};
+                           std::vector<uint64_t>(bg ? cl.n_pages : 0, ~0ull), {}, ~0ull, ~0ull, ~0ull};
     });
   }
   for (auto *set : {&clones, &bg_clones})

@@ -8,6 +8,8 @@
 //   fault_wait(ticket)                   wait for it
 //   evict(domain, pages, k, background)  queue an encrypt of k pages (not waited for);
 //                                        background: called by the evictor thread
+//   wait_evicted()                       wait for the client's latest own (overflow)
+//                                        eviction (sync_evict)
 //   drain()                              wait for every eviction queued
 // A page's requests reach the backend in the order of the window's changes
 // (fault_submit under the client's window lock; an eviction before any later
@@ -159,19 +161,25 @@ void run_client(Backend &be, const ms_window_config &cfg, ClientRun &cr) {
     if (rc == MS_OK) rc = be.fault_wait(ticket);  // the faulting thread is stalled until it is resolved
     if (rc != MS_OK) break;
     cr.lat_us.push_back(std::chrono::duration<double, std::micro>(clk::now() - f0).count());
-    std::lock_guard<std::mutex> lk(w.mu);
-    cr.st.faults += 1;
-    w.pages.push_back(pg);
-    w.members.insert(pg);
-    w.size.store(w.pages.size(), std::memory_order_relaxed);
-    if (w.pages.size() > cfg.window_pages) {  // overflow (without an evictor, or one running behind)
-      const size_t k = std::min<size_t>(cfg.evict_batch, w.pages.size());
-      std::vector<uint64_t> ev = take_oldest(w, k);
-      rc = be.evict(cl.domain, ev.data(), k, false);
-      if (rc != MS_OK) break;
-      count_eviction(cr, k, false);
+    bool evicted = false;
+    {
+      std::lock_guard<std::mutex> lk(w.mu);
+      cr.st.faults += 1;
+      w.pages.push_back(pg);
+      w.members.insert(pg);
+      w.size.store(w.pages.size(), std::memory_order_relaxed);
+      if (w.pages.size() > cfg.window_pages) {  // overflow (without an evictor, or one running behind)
+        const size_t k = std::min<size_t>(cfg.evict_batch, w.pages.size());
+        std::vector<uint64_t> ev = take_oldest(w, k);
+        rc = be.evict(cl.domain, ev.data(), k, false);
+        if (rc != MS_OK) break;
+        count_eviction(cr, k, false);
+        evicted = true;
+      }
+      if (bg && w.pages.size() > keep && w.evictor_asleep.load()) w.wake.notify_one();
     }
-    if (bg && w.pages.size() > keep && w.evictor_asleep.load()) w.wake.notify_one();
+    // the paper's server finishes a fault's eviction before it takes the next fault
+    if (evicted && cfg.sync_evict) rc = be.wait_evicted();
   }
   if (bg) {
     {

@@ -119,7 +119,7 @@ MS_SERVE_CONTINUOUS, MS_SERVE_ONE_PER_LAUNCH, MS_SERVE_ZERO_COPY = 0, 1, 2
 
 class ms_window_config(ctypes.Structure):
     _fields_ = [("window_pages", ctypes.c_uint32), ("evict_batch", ctypes.c_uint32),
-                ("background_free", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("background_free", ctypes.c_uint32), ("sync_evict", ctypes.c_uint32)]
 
 
 class ms_window_client(ctypes.Structure):
@@ -427,14 +427,14 @@ class Context:
         _check(_lib.ms_wait(self.handle, ticket, timeout_ms), "ms_wait")
 
     def run_window_clients(self, host_base, n_pages: int, window_pages: int, evict_batch: int, clients,
-                           timeout_ms: int = 60000, background_free: int = 0):
+                           timeout_ms: int = 60000, background_free: int = 0, sync_evict: bool = False):
         """Sliding-window clients served by ticketed launches, one clone of this
         context per client (its domain, its stream), in place on a pinned, mapped
         working set."""
         base = _ptr(host_base)
         return _run_window(lambda cfg, arr, n, st, fw: _lib.ms_window_run_ticketed(
             self.handle, base, n_pages, cfg, arr, n, st, fw, timeout_ms),
-            "ms_window_run_ticketed", window_pages, evict_batch, clients, background_free)
+            "ms_window_run_ticketed", window_pages, evict_batch, clients, background_free, sync_evict)
 
     def feed(self, capacity: int = 0, chunk: int = 0, wait_ms: int = 0, grab: int = 0) -> "Feed":
         return Feed(self, capacity, chunk, wait_ms, grab)
@@ -679,13 +679,14 @@ class Server:
         return lat, mk.value
 
     def run_window_clients(self, window_pages: int, evict_batch: int, clients, timeout_ms: int = 60000,
-                           background_free: int = 0):
+                           background_free: int = 0, sync_evict: bool = False):
         """Sliding-window clients: `clients` is a list of (domain, first_page, n_pages, trace).
         background_free = T > 0 adds a background evictor per client that keeps T
-        window slots free.  Returns (per-client stats dicts, per-client final
-        windows as lists of page indices)."""
+        window slots free; sync_evict makes each client wait for its own overflow
+        evictions.  Returns (per-client stats dicts, per-client final windows as
+        lists of page indices)."""
         return _run_window(lambda cfg, arr, n, st, fw: _lib.ms_window_run(self.handle, cfg, arr, n, st, fw, timeout_ms),
-                           "ms_window_run", window_pages, evict_batch, clients, background_free)
+                           "ms_window_run", window_pages, evict_batch, clients, background_free, sync_evict)
 
     def stats(self) -> dict:
         st = ms_server_stats()
@@ -707,8 +708,9 @@ class Server:
         self.destroy()
 
 
-def _run_window(call, name: str, window_pages: int, evict_batch: int, clients, background_free: int = 0):
-    cfg = ms_window_config(window_pages, evict_batch, background_free, 0)
+def _run_window(call, name: str, window_pages: int, evict_batch: int, clients, background_free: int = 0,
+                sync_evict: bool = False):
+    cfg = ms_window_config(window_pages, evict_batch, background_free, 1 if sync_evict else 0)
     arr = (ms_window_client * len(clients))()
     keep = []
     for i, (dom, first, n, trace) in enumerate(clients):
@@ -781,13 +783,13 @@ class Resident:
         return lat, mk.value
 
     def run_window_clients(self, host_base, n_pages: int, window_pages: int, evict_batch: int, clients,
-                           timeout_ms: int = 60000, background_free: int = 0):
+                           timeout_ms: int = 60000, background_free: int = 0, sync_evict: bool = False):
         """The sliding-window clients of Server.run_window_clients, served by these
         workers in place on a pinned, mapped working set of n_pages pages."""
         base = _ptr(host_base)
         return _run_window(lambda cfg, arr, n, st, fw: _lib.ms_window_run_resident(
             self.handle, base, n_pages, cfg, arr, n, st, fw, timeout_ms),
-            "ms_window_run_resident", window_pages, evict_batch, clients, background_free)
+            "ms_window_run_resident", window_pages, evict_batch, clients, background_free, sync_evict)
 
     def destroy(self) -> int:
         if self.handle:

@@ -289,3 +289,37 @@ def test_background_eviction_rejects_bad_thresholds(ms, key1):
             with pytest.raises(ms.MemShieldError) as e:
                 srv.run_window_clients(4, 1, [(1, 0, 32, tr)], background_free=free)
             assert e.value.code == ms.MS_EINVAL
+
+
+@pytest.mark.parametrize("backend", ["server", "resident", "ticketed"])
+@pytest.mark.parametrize("window,batch,free", [(8, 1, 0), (16, 4, 0), (8, 1, 3)])
+def test_synchronous_eviction_final_state(ms, key1, backend, window, batch, free):
+    """Each client waits for its own overflow evictions (the paper's per-client
+    server finishes an eviction before the next fault), alone and beside a
+    background evictor: the same final state as the asynchronous policies."""
+    per, n_clients = 128, 2
+    n = per * n_clients
+    plain = synth.page_bytes_fast(496, 0, n)
+    h = torch.from_numpy(plain.copy()).pin_memory()
+    doms = [801, 802]
+    clients = [(doms[c], c * per, per, synth.window_trace(497 + c, per, 1500)) for c in range(n_clients)]
+    kw = dict(background_free=free, sync_evict=True)
+    with ms.Context(key1) as ctx:
+        with ms.Server(ctx, h, n) as srv:
+            for c in range(n_clients):
+                srv.wait(srv.submit(ms.MS_ENCRYPT, np.arange(c * per, (c + 1) * per), domain=doms[c]))
+            if backend == "server":
+                stats, wins = srv.run_window_clients(window, batch, clients, **kw)
+        if backend == "resident":
+            with ms.Resident(ctx, workers=4) as res:
+                stats, wins = res.run_window_clients(h, n, window, batch, clients, **kw)
+        elif backend == "ticketed":
+            stats, wins = ctx.run_window_clients(h, n, window, batch, clients, **kw)
+    ws = h.numpy()
+    for c in range(n_clients):
+        st, win = stats[c], wins[c]
+        assert st["accesses"] == 1500 and st["faults"] - st["evictions"] == len(win) <= window - free
+        enc = np.array(sorted(set(range(c * per, (c + 1) * per)) - set(win)), dtype=np.uint64)
+        want = plain[c * per * PAGE:(c + 1) * per * PAGE].copy()
+        oracle.crypt_pages(key1, want, enc - np.uint64(c * per), enc, domain=doms[c])
+        assert np.array_equal(ws[c * per * PAGE:(c + 1) * per * PAGE], want), f"client {c}"

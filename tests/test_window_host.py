@@ -32,11 +32,21 @@ CASES = [
     (6, 4, 48, 2500, 32, 8, 31, 2),    # the evictor keeps one page at rest
     (7, 2, 40, 3000, 8, 9, 2, 1),      # overflow batches larger than the window
 ]
+SYNC_CASES = [  # the client waits for its own overflow evictions (the paper's server), with and without an evictor
+    (8, 2, 64, 3000, 8, 1, 0, 4),
+    (9, 3, 64, 3000, 8, 4, 2, 4),
+]
 
 
 @pytest.mark.parametrize("case", CASES)
 def test_window_invariants(sim, case):
     r = subprocess.run([sim] + [str(v) for v in case] + ["0"], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("case", SYNC_CASES)
+def test_window_invariants_with_synchronous_eviction(sim, case):
+    r = subprocess.run([sim] + [str(v) for v in case] + ["0", "1"], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.startswith("OK"), r.stdout + r.stderr
 
 

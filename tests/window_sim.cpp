@@ -17,6 +17,7 @@
 // "reorder" = 1 lets the executors run requests in any order, which must be
 // caught (the checks are not vacuous).
 // Usage: window_sim seed clients client_pages trace_len window evict_batch background_free executors reorder
+//        [sync_evict]
 #include <atomic>
 #include <condition_variable>
 #include <cstdio>
@@ -139,16 +140,27 @@ struct FakeBackend {
   FakeGpu *g;
   std::mutex emu;  // the client and its evictor both evict
   std::vector<uint64_t> evicts;
+  uint64_t own = ~0ull;  // the client's latest own eviction
   int fault_submit(uint32_t, uint64_t pg, uint64_t *ticket) {
     *ticket = g->submit(MS_DECRYPT, &pg, 1);
     return MS_OK;
   }
   int fault_wait(uint64_t t) { return g->wait(t); }
-  int evict(uint32_t, const uint64_t *pages, size_t k, bool) {
+  int evict(uint32_t, const uint64_t *pages, size_t k, bool background) {
     const uint64_t t = g->submit(MS_ENCRYPT, pages, k);
     std::lock_guard<std::mutex> lk(emu);
     evicts.push_back(t);
+    if (!background) own = t;
     return MS_OK;
+  }
+  int wait_evicted() {
+    uint64_t t;
+    {
+      std::lock_guard<std::mutex> lk(emu);
+      if (own == ~0ull) return MS_OK;
+      t = own;
+    }
+    return g->wait(t);
   }
   int drain() {
     for (uint64_t t : evicts) g->wait(t);
@@ -167,7 +179,7 @@ struct FakeBackend {
 }  // namespace
 
 int main(int argc, char **argv) {
-  if (argc != 10) return 2;
+  if (argc != 10 && argc != 11) return 2;
   const uint64_t seed = std::strtoull(argv[1], nullptr, 10);
   const int n_clients = std::atoi(argv[2]);
   const uint64_t per = std::strtoull(argv[3], nullptr, 10);
@@ -178,6 +190,7 @@ int main(int argc, char **argv) {
   cfg.background_free = (uint32_t)std::atoi(argv[7]);
   const int executors = std::atoi(argv[8]);
   const bool reorder = std::atoi(argv[9]) != 0;
+  cfg.sync_evict = argc == 11 ? (uint32_t)std::atoi(argv[10]) : 0;
 
   // traces: a small hot set with a sequential scan mixed in, so that pages
   // leave the window and come back while their evictions may still run
@@ -197,7 +210,7 @@ int main(int argc, char **argv) {
   for (int c = 0; c < n_clients; ++c) {
     runs[c].cl = &clients[c];
     th.emplace_back([&, c] {
-      FakeBackend be{&gpu, {}, {}};
+      FakeBackend be{&gpu, {}, {}, ~0ull};
       ms::window::run_client(be, cfg, runs[c]);
     });
   }
