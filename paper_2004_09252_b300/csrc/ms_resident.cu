@@ -547,8 +547,13 @@ extern "C" int ms_resident_replay(ms_resident *r, void *host_base, uint64_t n_pa
         __builtin_prefetch(&last_ticket[page_index[k]]);
     for (uint64_t k = offsets[q]; k < offsets[q + 1] && rc == MS_OK; ++k) {
       const uint64_t pg = page_index[k];
-      if (last_ticket[pg] != ~0ull) {
-        rc = ms_resident_wait(r, last_ticket[pg], timeout_ms);  // the page is still in flight
+      const uint64_t prev = last_ticket[pg];
+      // The page's previous request must be finished.  This thread is the
+      // only submitter during a replay, so it may read the done hint that its
+      // own submissions keep (no read of a GPU-written word); only a request
+      // that the hint does not cover is waited for.
+      if (prev != ~0ull && prev / W >= r->w[prev % W]->done_hint) {
+        rc = ms_resident_wait(r, prev, timeout_ms);  // the page may still be in flight
         if (rc != MS_OK) break;
       }
       ms_page_dom e{};
