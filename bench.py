@@ -1094,19 +1094,22 @@ def run_reference(args):
     oracle.build()
     threads = host_cores()
     key = synth.key_bytes(1)
-    cal_n = max(64, threads * 64)
-    cal = synth.page_bytes_fast(2, 0, cal_n)
-    ids = np.arange(cal_n, dtype=np.uint64)
-    oracle.crypt_pages(key, cal, ids, ids, threads=threads)          # first touch, thread start
-    t0 = time.perf_counter()
-    oracle.crypt_pages(key, cal, ids, ids, threads=threads)
-    per_page = (time.perf_counter() - t0) / cal_n                    # seconds per page, all threads
     budget = 150.0
-    steps = args.steps + args.warmup
-    npg = int(min(BULK_PAGES, max(threads * 4, budget / (steps * 2 * per_page))))
+    # the first warm-up step runs on the whole buffer and sets the sample: the
+    # whole buffer when the remaining steps fit in the budget, else a prefix
+    npg = BULK_PAGES
     buf = synth.page_bytes_fast(2, 0, npg)
     ids = np.arange(npg, dtype=np.uint64)
-    for _ in range(args.warmup):
+    t0 = time.perf_counter()
+    oracle.crypt_pages(key, buf, ids, ids, threads=threads)
+    oracle.crypt_pages(key, buf, ids, ids, threads=threads)
+    t_step = time.perf_counter() - t0
+    left = args.steps + args.warmup - 1
+    if left * t_step > budget:
+        npg = max(threads * 4, int(BULK_PAGES * budget / (left * t_step)))
+        buf = np.ascontiguousarray(buf[:npg * PAGE])
+        ids = ids[:npg]
+    for _ in range(args.warmup - 1):
         oracle.crypt_pages(key, buf, ids, ids, threads=threads)
         oracle.crypt_pages(key, buf, ids, ids, threads=threads)
     t0 = time.perf_counter()

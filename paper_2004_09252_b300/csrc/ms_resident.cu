@@ -203,12 +203,16 @@ inline void nap_ns(long ns) {
 inline uint64_t load_acq(const uint64_t *p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
 inline uint32_t load_acq32(const uint32_t *p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
 
+// The fields the submitting thread writes on every request (tail, the
+// hint, the lock) sit on a cache line of their own, apart from the pointers
+// that completion checks read, so that a completing thread does not pull
+// the submitter's line away on every check.
 struct Worker {
   RingEntry *h_ring = nullptr, *d_ring = nullptr;
   uint64_t *h_done = nullptr, *d_done = nullptr;
   WorkerShared *h_sh = nullptr, *d_sh = nullptr;
   cudaStream_t stream = nullptr;
-  uint64_t tail = 0;  // next local index to fill
+  alignas(64) uint64_t tail = 0;  // next local index to fill
   uint64_t done_hint = 0;  // every local index below this is known finished (under mu)
   std::mutex mu;
   uint64_t host_launches = 0;
@@ -462,6 +466,7 @@ extern "C" int ms_resident_replay(ms_resident *r, void *host_base, uint64_t n_pa
   }
   if (n > UINT32_MAX) return MS_ERANGE;
   const uint32_t W = r->cfg.workers;
+  const uint32_t R = r->cfg.ring_entries;
   const uint64_t total = offsets[n];
   // Completion is followed per worker, in ring order (a worker serves its
   // requests in order): each pass advances every worker's frontier over the
@@ -503,8 +508,11 @@ extern "C" int ms_resident_replay(ms_resident *r, void *host_base, uint64_t n_pa
       for (uint32_t w = 0; w < W; ++w) {
         const uint64_t hi = published[w].load(std::memory_order_acquire);
         while (frontier[w] < hi) {
-          const uint64_t ticket = (base_li[w] + frontier[w]) * W + w;
-          if (ms_resident_poll(r, ticket) != 1) break;
+          // the page's done word alone (ms_resident_poll would also read the
+          // worker's tail, the submitting thread's hot line); a later occupant
+          // of the slot means this one finished
+          const uint64_t li = base_li[w] + frontier[w];
+          if (load_acq(&r->w[w]->h_done[li & (R - 1)]) < li + 1) break;
           const uint32_t q = wmap[w][frontier[w]];
           if (--remaining[q] == 0) {
             latency_s[q] = (double)(int64_t)(now_ns() - sched[q]) * 1e-9;
@@ -560,10 +568,11 @@ extern "C" int ms_resident_replay(ms_resident *r, void *host_base, uint64_t n_pa
       e.addr = (uint64_t)dbase + pg * MS_PAGE_BYTES;
       e.page_id = pg;
       e.domain = domains ? domains[q] : r->ctx->cfg.domain;
-      const uint64_t spin_end = now_ns() + (uint64_t)timeout_ms * 1000000ull;
+      uint64_t spin_end = 0;  // set on the first MS_EBUSY: a full ring is rare
       for (;;) {
         rc = ms_resident_submit(r, &e, &tickets[k]);
         if (rc != MS_EBUSY) break;
+        if (!spin_end) spin_end = now_ns() + (uint64_t)timeout_ms * 1000000ull;
         if (now_ns() > spin_end) {
           rc = MS_ETIMEDOUT;
           break;
