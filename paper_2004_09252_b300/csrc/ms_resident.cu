@@ -524,7 +524,11 @@ extern "C" int ms_resident_replay(ms_resident *r, void *host_base, uint64_t n_pa
       }
       const uint64_t t = now_ns();
       if (progress) {
+        // pause briefly even after progress: a completer that re-reads the
+        // published counts without pause pulls their cache line away from
+        // the submitting thread on every page it publishes
         last_progress = t;
+        nap_ns(1000);
         continue;
       }
       if (t - last_progress > deadline_pad) {
