@@ -48,23 +48,24 @@ struct ServerBackend {
   std::mutex emu;  // evict_tickets: the client and its evictor both evict
   std::vector<uint64_t> evict_tickets;
   uint64_t last_own = ~0ull;  // the client's latest own eviction (written and read by the client)
-  int fault_submit(uint32_t domain, uint64_t pg, uint64_t *ticket) {
-    // an eviction of this page still in flight is waited for by the server's in-flight rule
+  // MS_EBUSY (every ticket slot pending) is retried until timeout_ms.
+  int submit(int op, uint32_t domain, const uint64_t *pages, size_t k, uint64_t *ticket) {
+    const auto limit = clk::now() + std::chrono::milliseconds(timeout_ms);
     for (;;) {
-      const int rc = ms_server_submit_dom(srv, MS_DECRYPT, domain, &pg, 1, ticket);
+      const int rc = ms_server_submit_dom(srv, op, domain, pages, (uint32_t)k, ticket);
       if (rc != MS_EBUSY) return rc;
+      if (clk::now() > limit) return MS_ETIMEDOUT;
       std::this_thread::yield();
     }
+  }
+  int fault_submit(uint32_t domain, uint64_t pg, uint64_t *ticket) {
+    // an eviction of this page still in flight is waited for by the server's in-flight rule
+    return submit(MS_DECRYPT, domain, &pg, 1, ticket);
   }
   int fault_wait(uint64_t ticket) { return ms_server_wait(srv, ticket, timeout_ms); }
   int evict(uint32_t domain, const uint64_t *pages, size_t k, bool background) {
     uint64_t ticket;
-    int rc;
-    for (;;) {
-      rc = ms_server_submit_dom(srv, MS_ENCRYPT, domain, pages, (uint32_t)k, &ticket);
-      if (rc != MS_EBUSY) break;
-      std::this_thread::yield();
-    }
+    const int rc = submit(MS_ENCRYPT, domain, pages, k, &ticket);
     if (rc == MS_OK) {
       std::lock_guard<std::mutex> lk(emu);
       evict_tickets.push_back(ticket);
