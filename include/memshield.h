@@ -439,11 +439,11 @@ typedef struct ms_server_config {
                                 a trickle of faults does not find it asleep) */
   uint32_t zero_copy_max_pages; /* continuous mode, working set in pinned mapped memory: the in-place
                                   lane.  While everything queued fits in this many pages (<= 512;
-                                  also capped by max_wave_pages),
+                                  also capped by max_wave_pages; 64 while a staged wave is in flight),
                                   the wave runs in place on the working set -- one launch with the
                                   entries in the kernel parameters, on its own stream, no staging
                                   copies -- and completes independently of staged waves.  Default
-                                  64 (any one request of the serving mix); 0 = every wave staged */
+                                  512; 0 = every wave staged */
 } ms_server_config;
 
 typedef struct ms_server_stats {

@@ -12,13 +12,14 @@
 // of slots; waves are freed in issue order.
 //
 // In-place lane (continuous mode, working set in pinned mapped memory,
-// zero_copy_max_pages = N > 0): while everything queued fits in N pages, the
-// server forms the wave without staging slots and runs it in place on the
-// working set: one launch on a stream of its own with the entries in the
-// kernel's parameters -- no gather, no copies, no scatter.  Such waves
-// complete as soon as their kernel does, independently of the staged waves
-// (up to kInplaceDepth at once); under load the queue outgrows N and waves
-// are staged as before.
+// zero_copy_max_pages = N > 0): while everything queued fits in N pages (64
+// while a staged wave is in flight), the server forms the wave without
+// staging slots and runs it in place on the working set: one launch on a
+// stream of its own with the entries in the kernel's parameters -- no
+// gather, no copies, no scatter.  Such waves complete as soon as their
+// kernel does, independently of the staged waves (up to kInplaceDepth at
+// once, one while a staged wave is in flight); under load the queue
+// outgrows N and waves are staged as before.
 #include <sys/prctl.h>
 #include <time.h>
 
@@ -156,7 +157,8 @@ struct Wave : ms::AdmittedWave {
   bool zc = false;  // run in place on the working set (no staging copies)
 };
 
-constexpr size_t kInplaceDepth = 4;  // in-place waves in flight at most
+constexpr size_t kInplaceDepth = 4;        // in-place waves in flight at most
+constexpr uint32_t kInplaceBusyPages = 64;  // in-place wave size while a staged wave is in flight
 
 }  // namespace
 
@@ -196,7 +198,7 @@ struct ms_server {
   Req &slot(uint64_t t) { return reqs[t % reqs.size()]; }
   void loop();
   bool form_wave(Wave &w);
-  bool form_inplace(Wave &w);
+  bool form_inplace(Wave &w, uint32_t max_pages);
   int issue(Wave &w);
   int issue_inplace(Wave &w);
   bool take_events(Wave &w);
@@ -227,10 +229,10 @@ bool ms_server::form_wave(Wave &w) {
   return ok;
 }
 
-bool ms_server::form_inplace(Wave &w) {
+bool ms_server::form_inplace(Wave &w, uint32_t max_pages) {
   std::lock_guard<std::mutex> lk(qmu);
   const bool ok = adm->form_inplace(incoming, [&](uint64_t t) -> const std::vector<uint64_t> & { return slot(t).pages; },
-                                    w, inplace_max);
+                                    w, max_pages);
   st_conflict.store(adm->conflict_waits);
   return ok;
 }
@@ -452,10 +454,18 @@ void ms_server::loop() {
         break;
       }
     }
+    // Kernels that reach the working set themselves move far less over the
+    // host link than the copy engines.  So while a staged wave is in flight
+    // (the load needs staging), the in-place lane narrows to one wave of at
+    // most kInplaceBusyPages pages: staging carries the bulk, and a short
+    // queue between staged waves still goes in place.
+    const bool staged_busy = !inflight.empty();
+    const uint32_t lane_pages = staged_busy ? std::min(inplace_max, kInplaceBusyPages) : inplace_max;
+    const size_t lane_depth = staged_busy ? 1 : kInplaceDepth;
     bool formed = false;
-    if (inplace_max && inflight_inplace.size() < kInplaceDepth && error.load() == 0) {
+    if (inplace_max && inflight_inplace.size() < lane_depth && error.load() == 0) {
       Wave w;
-      if (form_inplace(w)) {
+      if (form_inplace(w, lane_pages)) {
         int rc = issue_inplace(w);
         if (rc != MS_OK) {
           inflight_inplace.push_back(w);
@@ -516,7 +526,7 @@ void ms_server_config_default(ms_server_config *cfg) {
   cfg->mode = MS_SERVE_CONTINUOUS;
   cfg->max_request_pages = 4096;
   cfg->idle_spin_us = 20000;
-  cfg->zero_copy_max_pages = 64;  // the in-place lane takes any one request of the serving mix
+  cfg->zero_copy_max_pages = 512;  // the in-place lane: queues of up to 512 pages (its parameter limit)
 }
 
 static void free_server(ms_server *s) {
