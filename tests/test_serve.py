@@ -213,3 +213,38 @@ def test_pageable_working_set_is_staged(ms, key1):
         st = srv.stats()
     assert np.array_equal(ws, oracle_ws(key1, plain, pages.astype(np.uint64)))
     assert st["gather_ns"] > 0
+
+
+def test_in_place_lane_at_its_parameter_limit(ms, key1):
+    """One request of exactly 512 pages (the lane's kernel-parameter limit)
+    goes in place; one of 513 is staged; both match the oracle."""
+    n = 4096
+    h = working_set(79, n)
+    plain = h.numpy().copy()
+    p512 = synth.scattered_slots(80, n, 512)
+    rest = np.setdiff1d(np.arange(n), p512)
+    p513 = rest[synth.scattered_slots(81, len(rest), 513)]
+    with ms.Context(key1) as ctx, ms.Server(ctx, h, n) as srv:
+        srv.wait(srv.submit(ms.MS_ENCRYPT, p512))
+        st = srv.stats()
+        assert st["inplace_waves"] == 1 and st["max_wave_pages"] == 512
+        srv.wait(srv.submit(ms.MS_DECRYPT, p513))
+        st = srv.stats()
+        assert st["inplace_waves"] == 1 and st["waves"] == 2 and st["max_wave_pages"] == 513
+    touched = np.concatenate([p512, p513]).astype(np.uint64)
+    assert np.array_equal(h.numpy(), oracle_ws(key1, plain, touched))
+
+
+def test_destroy_with_in_place_waves_in_flight(ms, key1):
+    """Destroying a server right after queueing short requests waits (bounded)
+    for the in-place waves it issued and completes every request."""
+    n = 2048
+    h = working_set(82, n)
+    plain = h.numpy().copy()
+    pages = synth.scattered_slots(83, n, 400)
+    with ms.Context(key1) as ctx:
+        srv = ms.Server(ctx, h, n)
+        tickets = [srv.submit(ms.MS_ENCRYPT, pages[i:i + 4]) for i in range(0, 400, 4)]
+        assert srv.destroy() == ms.MS_OK
+    assert np.array_equal(h.numpy(), oracle_ws(key1, plain, pages.astype(np.uint64)))
+    assert len(tickets) == 100
