@@ -196,7 +196,7 @@ inline void nap_ns(long ns) {
     prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);
     slack_set = true;
   }
-  struct timespec ts = {0, ns};
+  struct timespec ts = {ns / 1000000000L, ns % 1000000000L};
   nanosleep(&ts, nullptr);
 }
 
@@ -551,7 +551,10 @@ extern "C" int ms_resident_replay(ms_resident *r, void *host_base, uint64_t n_pa
     for (;;) {
       const uint64_t t = now_ns();
       if (t >= target) break;
-      if (target - t > 200000) nap_ns((long)(target - t - 100000));
+      // sleep only through long gaps and wake 1 ms early, spin otherwise: an
+      // idle virtual CPU can wake milliseconds late, and a late submission
+      // counts as latency (arrivals are scheduled)
+      if (target - t > 2000000) nap_ns((long)(target - t - 1000000));
     }
     sched[q] = target;
     if (q + 1 < n)  // the next request's entries of the page-sized ticket table: hide their cache misses

@@ -49,7 +49,7 @@ inline uint64_t now_ns() {
 }
 
 inline void nap_ns(long ns) {
-  struct timespec ts = {0, ns};
+  struct timespec ts = {ns / 1000000000L, ns % 1000000000L};
   nanosleep(&ts, nullptr);
 }
 
@@ -746,7 +746,10 @@ int ms_server_replay(ms_server *s, size_t n, const double *arrival_s, const int 
     for (;;) {
       const uint64_t t = now_ns();
       if (t >= target) break;
-      if (target - t > 200000) nap_ns((long)(target - t - 100000));
+      // sleep only through long gaps and wake 1 ms early, spin otherwise: an
+      // idle virtual CPU can wake milliseconds late, and a late submission
+      // counts as latency (arrivals are scheduled)
+      if (target - t > 2000000) nap_ns((long)(target - t - 1000000));
     }
     const uint64_t n_pg = offsets[r + 1] - offsets[r];
     const uint64_t spin_limit = now_ns() + (uint64_t)timeout_ms * 1000000ull;
