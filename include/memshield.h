@@ -475,7 +475,9 @@ int ms_server_submit_dom(ms_server *srv, int op, uint32_t domain, const uint64_t
                          uint64_t *ticket);
 /* 1 = done (its pages are back in the working set), 0 = pending, < 0 = error. */
 int ms_server_poll(ms_server *srv, uint64_t ticket);
-/* Wait up to timeout_ms for the ticket: MS_OK, MS_ETIMEDOUT or an error. */
+/* Wait up to timeout_ms for the ticket: MS_OK, MS_ETIMEDOUT or an error.
+ * Polls with 1 us naps for about 50 us, then blocks; the calling thread's
+ * timer slack is set to 1 us on its first nap so that the naps stay short. */
 int ms_server_wait(ms_server *srv, uint64_t ticket, uint32_t timeout_ms);
 /*
  * Open-loop replay, for measurement: request r (op ops[r], domain domains[r]

@@ -48,7 +48,15 @@ inline uint64_t now_ns() {
   return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(clk::now().time_since_epoch()).count();
 }
 
+// Short naps must stay short: the first nap on a thread (the server's, a
+// replay's or a caller of ms_server_wait) drops its timer slack (default
+// 50 us, which would stretch a 1 us nap to about 50 us) to 1 us.
 inline void nap_ns(long ns) {
+  thread_local bool slack_set = false;
+  if (!slack_set) {
+    prctl(PR_SET_TIMERSLACK, 1000UL, 0, 0, 0);
+    slack_set = true;
+  }
   struct timespec ts = {ns / 1000000000L, ns % 1000000000L};
   nanosleep(&ts, nullptr);
 }
