@@ -437,9 +437,10 @@ def run_ours(args):
             "autotune": br["autotune"]}
     if not args.no_serving and world == 1:
         rows, setup_s = serve_rows(args, args.serve_rates, ["continuous", "one_per_launch", "resident"],
-                                   args.serve_seconds, one_per_launch_cap=args.one_per_launch_cap)
+                                   args.serve_seconds, one_per_launch_cap=args.one_per_launch_cap,
+                                   reps_below=(1e5, args.low_rate_reps))
         keep = ("offered_pages_per_s", "mode", "requests", "arrival_s", "sustained_pages_per_s", "p50_us", "p99_us",
-                "p999_us", "first_second", "steady", "p99_us_by_second", "max_submit_lag_ms")
+                "p999_us", "reps", "p99_us_each", "first_second", "steady", "p99_us_by_second", "max_submit_lag_ms")
         one = {r["offered_pages_per_s"]: r for r in rows if r["mode"] == "one_per_launch"}
 
         def p99(r):  # the steady state where the run has one, else the whole run
@@ -448,6 +449,7 @@ def run_ours(args):
             "workload": SERVE_WORKLOAD.format(n=args.serve_pages, gib=args.serve_pages * PAGE / 2**30,
                                               sec=args.serve_seconds)
             + f"; one launch per request capped at {args.one_per_launch_cap} requests (>= 50k requests)"
+            + f"; rates under 100k run {args.low_rate_reps} times (medians; every run in p99_us_each)"
             + (f"; {args.serve_warmup_s:g} s of separate requests replayed untimed before each run"
                if args.serve_warmup_s > 0 else ""),
             "working_set_setup_s": round(setup_s, 1),
@@ -879,10 +881,12 @@ def latency_split(arrival, lat):
     return out
 
 
-def serve_rows(args, rates, modes, seconds, one_per_launch_cap=None):
+def serve_rows(args, rates, modes, seconds, one_per_launch_cap=None, reps_below=None):
     """Replay the serving workload at each rate in each mode; one row per (rate, mode).
     Each run covers `seconds` of arrivals; one_per_launch_cap (requests) bounds
-    the one-launch-per-request runs, which saturate far below the top rates."""
+    the one-launch-per-request runs, which saturate far below the top rates.
+    reps_below = (rate, k): rates under `rate` run k times (medians reported),
+    where a single spoiled second weighs most."""
     import numpy as np
     import torch
 
@@ -914,7 +918,10 @@ def serve_rows(args, rates, modes, seconds, one_per_launch_cap=None):
             offsets = w_offsets[:n_req + 1]
             pages = w_pages[:int(offsets[-1])]
             reps = []
-            for _ in range(max(1, args.serve_reps)):
+            n_reps = max(1, args.serve_reps)
+            if reps_below and rate < reps_below[0]:
+                n_reps = max(n_reps, reps_below[1])
+            for _ in range(n_reps):
                 if name == "resident" and args.resident_submitters > 1:
                     lat, makespan, total_mt = resident_multi(args, ms, ctx, ws, n, rate, seconds)
                     st = {"waves": total_mt, "max_wave_requests": 1, "conflict_waits": 0, "budget_waits": 0,
@@ -958,13 +965,19 @@ def serve_rows(args, rates, modes, seconds, one_per_launch_cap=None):
                                                                       "p999_us")}
             mid = reps[len(reps) // 2]
             st = mid["st"]
+
+            def split_median(part):  # each latency figure of a part: the median over the repetitions
+                vals = [r["split"][part] for r in reps if r["split"] and r["split"][part]]
+                if not vals:
+                    return None
+                return {k: (vals[0][k] if k == "requests" else round(float(np.median([v[k] for v in vals])), 1))
+                        for k in vals[0]}
             rows.append({"offered_pages_per_s": rate, "mode": name, "requests": n_req, "pages": total,
                          "arrival_s": round(float(arrival[-1]), 2),
                          "sustained_pages_per_s": round(med["sustained_pages_per_s"], 1),
                          "p50_us": round(med["p50_us"], 1), "p99_us": round(med["p99_us"], 1),
                          "p999_us": round(med["p999_us"], 1), "reps": len(reps),
-                         "first_second": mid["split"]["first_second"] if mid["split"] else None,
-                         "steady": mid["split"]["steady"] if mid["split"] else None,
+                         "first_second": split_median("first_second"), "steady": split_median("steady"),
                          "p99_us_each": [round(r["p99_us"], 1) for r in reps],
                          "p99_us_by_second": [r["by_sec"] for r in reps],
                          "max_submit_lag_ms": [r["st"].get("submit_lag_ms") for r in reps],
@@ -1162,6 +1175,8 @@ def main():
     ap.add_argument("--serve-warmup-s", type=float, default=0.3,
                     help="serving: replay this many seconds of a separate request stream (seed 55) at the same "
                          "rate, untimed, before each measured run")
+    ap.add_argument("--low-rate-reps", type=int, default=3,
+                    help="default line: repetitions of the rates under 100k pages/s (medians reported)")
     ap.add_argument("--one-per-launch-cap", type=int, default=50000,
                     help="serving: requests per one-launch-per-request run at most (it saturates near 270k pages/s)")
     ap.add_argument("--copy-threads", type=int, default=8)
