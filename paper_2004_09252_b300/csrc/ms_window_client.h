@@ -201,7 +201,7 @@ void run_client(Backend &be, const ms_window_config &cfg, ClientRun &cr) {
   cr.final_window.assign(w.pages.begin(), w.pages.end());
 }
 
-double percentile(std::vector<double> v, double q) {
+inline double percentile(std::vector<double> v, double q) {
   if (v.empty()) return 0.0;
   std::sort(v.begin(), v.end());
   const double pos = q * (double)(v.size() - 1);
