@@ -338,11 +338,11 @@ int ms_resident_create(ms_ctx *c, const ms_resident_config *cfg_in, ms_resident 
   return MS_OK;
 }
 
-int ms_resident_submit(ms_resident *r, const ms_page_dom *page, uint64_t *ticket) {
-  if (!r || !page || !ticket) return MS_EINVAL;
-  if (page->addr == 0 || (page->addr & 15u)) return MS_EINVAL;
+namespace {
+
+// Queue one page on worker wi (MS_EBUSY when its ring slot is still taken).
+int submit_to(ms_resident *r, int wi, const ms_page_dom *page, uint64_t *ticket) {
   const uint32_t W = r->cfg.workers;
-  const int wi = (int)(r->rr.fetch_add(1) % W);
   Worker &w = *r->w[wi];
   std::lock_guard<std::mutex> lk(w.mu);
   const uint64_t li = w.tail;
@@ -372,6 +372,16 @@ int ms_resident_submit(ms_resident *r, const ms_page_dom *page, uint64_t *ticket
   if (rc != MS_OK) return rc;
   *ticket = li * W + (uint64_t)wi;
   return MS_OK;
+}
+
+bool page_ok(const ms_page_dom *page) { return page->addr != 0 && (page->addr & 15u) == 0; }
+
+}  // namespace
+
+int ms_resident_submit(ms_resident *r, const ms_page_dom *page, uint64_t *ticket) {
+  if (!r || !page || !ticket) return MS_EINVAL;
+  if (!page_ok(page)) return MS_EINVAL;
+  return submit_to(r, (int)(r->rr.fetch_add(1) % r->cfg.workers), page, ticket);
 }
 
 int ms_resident_poll(ms_resident *r, uint64_t ticket) {
@@ -575,9 +585,17 @@ extern "C" int ms_resident_replay(ms_resident *r, void *host_base, uint64_t n_pa
       e.addr = (uint64_t)dbase + pg * MS_PAGE_BYTES;
       e.page_id = pg;
       e.domain = domains ? domains[q] : r->ctx->cfg.domain;
+      // Pages go to the workers in strict rotation, and a page whose worker
+      // has a full ring waits for that worker: passing it to the next one
+      // would give some worker more than its share of the replay's pages.
+      if (!page_ok(&e)) {
+        rc = MS_EINVAL;
+        break;
+      }
+      const int wi = (int)(r->rr.fetch_add(1) % W);
       uint64_t spin_end = 0;  // set on the first MS_EBUSY: a full ring is rare
       for (;;) {
-        rc = ms_resident_submit(r, &e, &tickets[k]);
+        rc = submit_to(r, wi, &e, &tickets[k]);
         if (rc != MS_EBUSY) break;
         if (!spin_end) spin_end = now_ns() + (uint64_t)timeout_ms * 1000000ull;
         if (now_ns() > spin_end) {

@@ -124,6 +124,27 @@ def test_replay_matches_oracle(ms, key1):
     assert np.array_equal(h.numpy(), want)
 
 
+@pytest.mark.parametrize("workers,ring", [(16, 4), (32, 64)])
+def test_replay_full_rings(ms, key1, workers, ring):
+    """Every request arrives at once, so the rings fill and the replay waits
+    for room on the worker whose turn it is: the pages still go round the
+    workers in rotation, and the result matches the oracle."""
+    n, n_req = 4096, 3000
+    _, _, offsets, pages = synth.serving_workload(119, n_req, 2e5, n)
+    arrival = np.zeros(n_req)
+    plain = synth.page_bytes_fast(120, 0, n)
+    h = torch.from_numpy(plain.copy()).pin_memory()
+    with ms.Context(key1) as ctx, ms.Resident(ctx, workers=workers, ring_entries=ring) as res:
+        lat, makespan = res.replay(h, n, arrival, offsets, pages)
+        st = res.stats()
+    assert (lat >= 0).all() and makespan > 0 and st["requests"] == int(offsets[-1])
+    counts = np.bincount(pages.astype(np.int64), minlength=n)
+    odd = np.nonzero(counts % 2)[0].astype(np.uint64)
+    want = plain.copy()
+    oracle.crypt_pages(key1, want, odd, odd)
+    assert np.array_equal(h.numpy(), want)
+
+
 def test_config_checks(ms, key1):
     with ms.Context(key1, rounds=12) as ctx:
         with pytest.raises(ms.MemShieldError):
