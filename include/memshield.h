@@ -417,13 +417,22 @@ int ms_tune_load(ms_ctx *ctx, const char *path);
  */
 typedef struct ms_server ms_server;
 
-/* Continuous mode stages its waves, except that (zero_copy_max_pages) it runs
- * small waves in place when the queue is short; MS_SERVE_ONE_PER_LAUNCH
- * always stages.
+/* MS_SERVE_CONTINUOUS over pinned, mapped memory with zero_copy_max_pages > 0
+ * (the default): no wave is staged.  Short queues go through the in-place
+ * lane (entries in the kernel parameters); longer ones form waves whose
+ * entries take staging slots while their pages stay in place, as in
+ * MS_SERVE_ZERO_COPY.  Over pageable memory, or with zero_copy_max_pages = 0,
+ * every wave is staged as described above.  MS_SERVE_ONE_PER_LAUNCH always
+ * stages.
  * MS_SERVE_ZERO_COPY: no staging copies; the kernel reads and writes the
  * working set directly over the host link (it must be pinned, mapped memory,
  * e.g. from cudaHostAlloc); the staging budget then only bounds the pages in
- * flight.  Requests are admitted the same way. */
+ * flight.  Requests are admitted the same way.
+ * Every kernel that works on the working set in place runs on one stream of
+ * the server, with a bounded grid (16 CTAs of 512 threads), the next
+ * keystream block's bytes loaded while the current one is computed: on B300
+ * that moves about 32 GB/s each way over the host link, where a grid of one
+ * thread per block stays near 7.5 GB/s. */
 enum ms_serve_mode { MS_SERVE_CONTINUOUS = 0, MS_SERVE_ONE_PER_LAUNCH = 1, MS_SERVE_ZERO_COPY = 2 };
 
 typedef struct ms_server_config {
@@ -439,11 +448,11 @@ typedef struct ms_server_config {
                                 a trickle of faults does not find it asleep) */
   uint32_t zero_copy_max_pages; /* continuous mode, working set in pinned mapped memory: the in-place
                                   lane.  While everything queued fits in this many pages (<= 512;
-                                  also capped by max_wave_pages; 64 while a staged wave is in flight),
+                                  also capped by max_wave_pages; 64 while a longer wave is in flight),
                                   the wave runs in place on the working set -- one launch with the
-                                  entries in the kernel parameters, on its own stream, no staging
-                                  copies -- and completes independently of staged waves.  Default
-                                  512; 0 = every wave staged */
+                                  entries in the kernel parameters, no entry copy -- and completes
+                                  independently of the longer waves, which run in place too (see
+                                  ms_serve_mode).  Default 512; 0 = lane off and every wave staged */
 } ms_server_config;
 
 typedef struct ms_server_stats {
@@ -458,6 +467,7 @@ typedef struct ms_server_stats {
   uint64_t gather_ns;        /* server-thread time spent copying pages into staging */
   uint64_t scatter_ns;       /* ... and back into the working set */
   uint64_t inplace_waves;    /* waves run through the in-place lane (included in waves) */
+  uint64_t staged_waves;     /* waves whose pages were copied through staging (included in waves) */
 } ms_server_stats;
 
 void ms_server_config_default(ms_server_config *cfg);

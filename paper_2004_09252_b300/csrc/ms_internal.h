@@ -124,6 +124,14 @@ template <typename E>
 size_t inline_max_pages();
 template <typename E>
 cudaError_t launch_pages_inline(const ms_ctx *c, const E *pages, size_t n, cudaStream_t s);
+// K1 for pages in pinned, mapped host memory (every access crosses the host
+// link): a bounded grid striding over the pages' blocks, the next block
+// loaded while the current one is computed.  launch_pages_link carries the
+// entries in the kernel parameters (n <= link_param_max_pages() = 512);
+// launch_pages_link_dev reads them from device memory.
+size_t link_param_max_pages();
+cudaError_t launch_pages_link(const ms_ctx *c, const ms_page_dom *pages, size_t n, cudaStream_t s);
+cudaError_t launch_pages_link_dev(const ms_ctx *c, const ms_page_dom *d_pages, size_t n, cudaStream_t s);
 int k1_shape_count();
 void k1_shape(int i, int *rounds, Tune *t);
 

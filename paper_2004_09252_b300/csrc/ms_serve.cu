@@ -13,13 +13,15 @@
 //
 // In-place lane (continuous mode, working set in pinned mapped memory,
 // zero_copy_max_pages = N > 0): while everything queued fits in N pages (64
-// while a staged wave is in flight), the server forms the wave without
-// staging slots and runs it in place on the working set: one launch on a
-// stream of its own with the entries in the kernel's parameters -- no
-// gather, no copies, no scatter.  Such waves complete as soon as their
-// kernel does, independently of the staged waves (up to kInplaceDepth at
-// once, one while a staged wave is in flight); under load the queue
-// outgrows N and waves are staged as before.
+// while a longer wave is in flight), the server forms the wave without
+// staging slots and runs it in place on the working set: one launch of the
+// host-link page kernel (a bounded grid, ms_link.cu) with the entries in the
+// kernel's parameters -- no gather, no copies, no scatter.  Such waves
+// complete as soon as their kernel does (up to kInplaceDepth at once, one
+// while a longer wave is in flight).  Under load the queue outgrows N, and
+// the longer waves run in place as well: their entries take staging slots
+// (copied to the device), their pages do not.  Only a pageable working set,
+// or N = 0, has its pages gathered, copied both ways and scattered.
 #include <sys/prctl.h>
 #include <time.h>
 
@@ -166,7 +168,7 @@ struct Wave : ms::AdmittedWave {
 };
 
 constexpr size_t kInplaceDepth = 4;        // in-place waves in flight at most
-constexpr uint32_t kInplaceBusyPages = 64;  // in-place wave size while a staged wave is in flight
+constexpr uint32_t kInplaceBusyPages = 64;  // lane wave size while a longer wave is in flight
 
 }  // namespace
 
@@ -179,7 +181,10 @@ struct ms_server {
   uint8_t *h_stage = nullptr, *d_stage = nullptr;
   ms_page_dom *h_ent = nullptr, *d_ent = nullptr;
   cudaStream_t s_in = nullptr, s_work[2] = {nullptr, nullptr};
-  cudaStream_t s_fast = nullptr;  // the in-place lane
+  // Kernels that work on the mapped working set itself (in-place lane,
+  // zero-copy waves) run on this one stream: one such kernel at a time, so the
+  // host link sees at most one bounded grid of SM-issued accesses.
+  cudaStream_t s_link = nullptr;
   uint32_t inplace_max = 0;       // pages of an in-place wave at most (0: lane off)
   std::vector<Req> reqs;
   std::mutex qmu;
@@ -199,7 +204,7 @@ struct ms_server {
   std::mutex done_mu;
   std::condition_variable done_cv;
   std::atomic<uint64_t> st_req{0}, st_pages{0}, st_waves{0}, st_maxreq{0}, st_maxpages{0}, st_conflict{0},
-      st_budget{0}, st_maxstaged{0}, st_gather_ns{0}, st_scatter_ns{0}, st_inplace{0};
+      st_budget{0}, st_maxstaged{0}, st_gather_ns{0}, st_scatter_ns{0}, st_inplace{0}, st_staged{0};
   uint64_t d_host = 0;  // device address of host_base (zero-copy mode)
   uint64_t idle_spin_ns = 0;
 
@@ -280,8 +285,8 @@ int ms_server::issue_inplace(Wave &w) {
   }
   w.zc = true;
   cudaError_t e = injected(MS_FAULT_SERVER);
-  if (e == cudaSuccess) e = launch_pages_inline(ctx, ent, k, s_fast);
-  if (e == cudaSuccess) e = cudaEventRecord(w.ev_done, s_fast);
+  if (e == cudaSuccess) e = launch_pages_link(ctx, ent, k, s_link);
+  if (e == cudaSuccess) e = cudaEventRecord(w.ev_done, s_link);
   if (e != cudaSuccess) return cuda_fail(ctx, e);
   st_waves.fetch_add(1);
   st_inplace.fetch_add(1);
@@ -304,9 +309,12 @@ int ms_server::issue(Wave &w) {
       map.push_back({pg, k++});
     }
   }
-  // zero-copy mode: the kernel works on the working set itself (small waves
-  // of continuous mode go through the in-place lane instead, issue_inplace)
-  const bool zc = cfg.mode == MS_SERVE_ZERO_COPY;
+  // Zero-copy mode, and continuous mode whenever its in-place lane is on (a
+  // pinned, mapped working set): the kernel works on the working set itself,
+  // on the link stream, and only the entries use the wave's staging slots
+  // (short queues of continuous mode take the lane instead, issue_inplace).
+  // Otherwise the pages are gathered into staging and copied both ways.
+  const bool zc = cfg.mode == MS_SERVE_ZERO_COPY || inplace_max != 0;
   w.zc = zc;
   const uint64_t tg = now_ns();
   if (zc) {  // the kernel works on the working set itself, through the host link
@@ -325,14 +333,15 @@ int ms_server::issue(Wave &w) {
   }
   st_gather_ns.fetch_add(now_ns() - tg);
   const size_t off = (size_t)w.pos * MS_PAGE_BYTES, bytes = (size_t)w.len * MS_PAGE_BYTES;
-  cudaStream_t sw = s_work[wave_seq++ & 1];
+  cudaStream_t sw = zc ? s_link : s_work[wave_seq++ & 1];
   cudaError_t e = injected(MS_FAULT_SERVER);
   if (e == cudaSuccess && !zc) e = cudaMemcpyAsync(d_stage + off, h_stage + off, bytes, cudaMemcpyHostToDevice, s_in);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_ent + w.pos, h_ent + w.pos, sizeof(ms_page_dom) * w.len, cudaMemcpyHostToDevice, s_in);
   if (e == cudaSuccess) e = cudaEventRecord(w.ev_h2d, s_in);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(sw, w.ev_h2d, 0);
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && zc) e = launch_pages_link_dev(ctx, d_ent + w.pos, w.len, sw);
+  if (e == cudaSuccess && !zc) {
     PageArgs a = make_args(ctx);
     a.dpages = d_ent + w.pos;
     a.n_pages = w.len;
@@ -343,6 +352,7 @@ int ms_server::issue(Wave &w) {
   if (e == cudaSuccess) e = cudaEventRecord(w.ev_done, sw);
   if (e != cudaSuccess) return cuda_fail(ctx, e);
   st_waves.fetch_add(1);
+  if (!zc) st_staged.fetch_add(1);
   atomic_max(st_maxreq, w.tickets.size());
   atomic_max(st_maxpages, w.len);
   return MS_OK;
@@ -462,14 +472,13 @@ void ms_server::loop() {
         break;
       }
     }
-    // Kernels that reach the working set themselves move far less over the
-    // host link than the copy engines.  So while a staged wave is in flight
-    // (the load needs staging), the in-place lane narrows to one wave of at
-    // most kInplaceBusyPages pages: staging carries the bulk, and a short
-    // queue between staged waves still goes in place.
-    const bool staged_busy = !inflight.empty();
-    const uint32_t lane_pages = staged_busy ? std::min(inplace_max, kInplaceBusyPages) : inplace_max;
-    const size_t lane_depth = staged_busy ? 1 : kInplaceDepth;
+    // While a longer wave is in flight (the load outgrew the lane), the lane
+    // narrows to one wave of at most kInplaceBusyPages pages: the longer
+    // waves carry the bulk, and a short queue between them still goes
+    // through the lane.
+    const bool long_busy = !inflight.empty();
+    const uint32_t lane_pages = long_busy ? std::min(inplace_max, kInplaceBusyPages) : inplace_max;
+    const size_t lane_depth = long_busy ? 1 : kInplaceDepth;
     bool formed = false;
     if (inplace_max && inflight_inplace.size() < lane_depth && error.load() == 0) {
       Wave w;
@@ -545,7 +554,7 @@ static void free_server(ms_server *s) {
     cudaEventDestroy(p.second);
   }
   if (s->s_in) cudaStreamDestroy(s->s_in);
-  if (s->s_fast) cudaStreamDestroy(s->s_fast);
+  if (s->s_link) cudaStreamDestroy(s->s_link);
   for (auto &w : s->s_work)
     if (w) cudaStreamDestroy(w);
   if (s->h_stage) cudaFreeHost(s->h_stage);
@@ -607,10 +616,10 @@ int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_serv
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_work[0], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_work[1], cudaStreamNonBlocking);
-  if (e == cudaSuccess && s->inplace_max) {
-    int lo = 0, hi = 0;  // the in-place lane's stream at the highest priority: a fault waits on it
+  if (e == cudaSuccess && (s->inplace_max || cfg.mode == MS_SERVE_ZERO_COPY)) {
+    int lo = 0, hi = 0;  // the link stream at the highest priority: a fault waits on it
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    e = cudaStreamCreateWithPriority(&s->s_fast, cudaStreamNonBlocking, hi);
+    e = cudaStreamCreateWithPriority(&s->s_link, cudaStreamNonBlocking, hi);
   }
   if (e != cudaSuccess) {
     free_server(s);
@@ -806,6 +815,7 @@ int ms_server_get_stats(const ms_server *s, ms_server_stats *out) {
   out->gather_ns = s->st_gather_ns.load();
   out->scatter_ns = s->st_scatter_ns.load();
   out->inplace_waves = s->st_inplace.load();
+  out->staged_waves = s->st_staged.load();
   return MS_OK;
 }
 
@@ -824,7 +834,7 @@ int ms_server_destroy(ms_server *s) {
       int r = wait_event(s->ctx, w.ev_done, s->ctx->cfg.timeout_ms);
       if (r != MS_OK) return r;  // still running on the GPU: leave the buffers allocated
     }
-  for (cudaStream_t st : {s->s_in, s->s_work[0], s->s_work[1], s->s_fast}) {
+  for (cudaStream_t st : {s->s_in, s->s_work[0], s->s_work[1], s->s_link}) {
     if (!st) continue;
     cudaEvent_t ev;
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return cuda_fail(s->ctx, cudaGetLastError());

@@ -111,7 +111,8 @@ class ms_server_config(ctypes.Structure):
 class ms_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("requests_done", "pages_done", "waves", "max_wave_requests",
                                                "max_wave_pages", "conflict_waits", "budget_waits",
-                                               "max_staged_pages", "gather_ns", "scatter_ns", "inplace_waves")]
+                                               "max_staged_pages", "gather_ns", "scatter_ns", "inplace_waves",
+                                               "staged_waves")]
 
 
 MS_SERVE_CONTINUOUS, MS_SERVE_ONE_PER_LAUNCH, MS_SERVE_ZERO_COPY = 0, 1, 2

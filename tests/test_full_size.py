@@ -41,11 +41,13 @@ def test_host_config_4gib(ms, key1):
     assert np.array_equal(h.numpy(), want)
 
 
-@pytest.mark.parametrize("form,rate,n_req", [("continuous", 1.41e5, 17625), ("resident", 2e6, 250000)])
+@pytest.mark.parametrize("form,rate,n_req", [("continuous", 1.41e5, 17625), ("continuous", 2e6, 250000),
+                                             ("resident", 2e6, 250000)])
 def test_serving_config_16gib(ms, key1, form, rate, n_req):
     """The serving mix over the 16 GiB working set (seed 5): one second at
-    141k pages/s through continuous batching, and one second at 2M pages/s
-    through resident workers (8 workers, in place).  The whole 16 GiB result
+    141k pages/s and one at 2M pages/s through continuous batching (in-place
+    lane and entry-list waves), and one second at 2M pages/s through resident
+    workers (8 workers, in place).  The whole 16 GiB result
     equals the closed form computed by the oracle (a page applied an odd
     number of times is encrypted, every other page unchanged), byte for byte
     and by SHA-256, and a seeded 1/16 of the touched pages, recomputed one by

@@ -83,15 +83,38 @@ def test_alone_equals_mix(ms, key1, mode, zc_pages, rate):
         assert np.array_equal(a[sel], b[sel]), f"request {r} differs alone vs mix"
     assert np.array_equal(alone.numpy(), oracle_ws(key1, plain, pages))
     if mode == 1:
-        assert st["max_wave_requests"] == 1 and st["waves"] == n_req
+        assert st["max_wave_requests"] == 1 and st["waves"] == n_req and st["staged_waves"] == n_req
     elif mode == 2:
-        assert st["gather_ns"] < st["waves"] * 10**6      # no staging copies in zero-copy mode
+        assert st["staged_waves"] == 0                    # no staging copies in zero-copy mode
     else:
         assert st["waves"] <= n_req
+        # continuous mode over mapped memory stages only with the lane off
+        assert st["staged_waves"] == (st["waves"] if zc_pages == 0 else 0)
     if mode != 0 or zc_pages == 0:                        # the in-place lane is continuous mode's only
         assert st["inplace_waves"] == 0
     elif rate < 1e6:                                      # short queues: the lane carries waves
         assert 0 < st["inplace_waves"] <= st["waves"]
+
+
+@pytest.mark.parametrize("rounds", [20, 12, 8])
+def test_zero_copy_large_waves(ms, key1, rounds):
+    """Every request arrives at once, so zero-copy waves hold hundreds to
+    thousands of pages: the bounded-grid kernel that works on the mapped
+    working set takes several blocks per thread, with a ragged last step.
+    The working set equals the oracle's, for each round count."""
+    n, n_req = 16384, 1200
+    _, ops, offsets, pages = distinct_workload(78, n_req, n, 2e6)
+    arrival = np.zeros(n_req)
+    plain = synth.page_bytes_fast(79, 0, n)
+    h = torch.from_numpy(plain.copy()).pin_memory()
+    with ms.Context(key1, rounds=rounds) as ctx, ms.Server(ctx, h, n, mode=ms.MS_SERVE_ZERO_COPY) as srv:
+        lat, makespan = srv.replay(arrival, ops, offsets, pages)
+        st = srv.stats()
+    assert (lat >= 0).all() and makespan > 0
+    assert st["pages_done"] == int(offsets[-1]) and st["max_wave_pages"] > 256
+    want = plain.copy()
+    oracle.crypt_pages(key1, want, pages, pages, rounds=rounds, threads=8)
+    assert np.array_equal(h.numpy(), want)
 
 
 def test_conflicting_requests_serialise(ms, key1):
@@ -119,9 +142,10 @@ def test_conflicting_requests_serialise(ms, key1):
 
 def test_in_place_lane_with_conflicts(ms, key1):
     """Requests submitted a few at a time on overlapping pages, with the
-    in-place lane on: short queues go in place, longer ones are staged, and a
-    request on a page still in flight in either lane waits for it.  The final
-    state is the closed form of the application counts."""
+    in-place lane on: short queues go through the lane, longer ones form
+    entry-list waves (in place as well), and a request on a page still in
+    flight in either kind of wave waits for it.  The final state is the
+    closed form of the application counts."""
     n = 512
     h = working_set(76, n)
     plain = h.numpy().copy()
@@ -131,7 +155,7 @@ def test_in_place_lane_with_conflicts(ms, key1):
         pending = []
         for r in range(600):
             x = int(rng[r] % np.uint64(64))
-            # every fifth request is 20 pages (always staged), the others one page
+            # every fifth request is 20 pages (never in the 16-page lane), the others one page
             sel = (x + np.arange(20)) % 64 if r % 5 == 0 else np.array([x])
             counts[sel] += 1
             pending.append(srv.submit(r % 2, sel))
@@ -142,7 +166,7 @@ def test_in_place_lane_with_conflicts(ms, key1):
         st = srv.stats()
     odd = np.nonzero(counts % 2)[0].astype(np.uint64)
     assert np.array_equal(h.numpy(), oracle_ws(key1, plain, odd))
-    assert st["inplace_waves"] > 0 and st["waves"] > st["inplace_waves"]
+    assert st["inplace_waves"] > 0 and st["waves"] > st["inplace_waves"] and st["staged_waves"] == 0
 
 
 def test_in_place_lane_limit(ms, key1):
@@ -212,12 +236,13 @@ def test_pageable_working_set_is_staged(ms, key1):
             srv.wait(t)
         st = srv.stats()
     assert np.array_equal(ws, oracle_ws(key1, plain, pages.astype(np.uint64)))
-    assert st["gather_ns"] > 0
+    assert st["gather_ns"] > 0 and st["staged_waves"] == st["waves"] > 0 and st["inplace_waves"] == 0
 
 
 def test_in_place_lane_at_its_parameter_limit(ms, key1):
     """One request of exactly 512 pages (the lane's kernel-parameter limit)
-    goes in place; one of 513 is staged; both match the oracle."""
+    goes through the lane; one of 513 forms an entry-list wave, in place as
+    well; both match the oracle."""
     n = 4096
     h = working_set(79, n)
     plain = h.numpy().copy()
@@ -231,6 +256,7 @@ def test_in_place_lane_at_its_parameter_limit(ms, key1):
         srv.wait(srv.submit(ms.MS_DECRYPT, p513))
         st = srv.stats()
         assert st["inplace_waves"] == 1 and st["waves"] == 2 and st["max_wave_pages"] == 513
+        assert st["staged_waves"] == 0
     touched = np.concatenate([p512, p513]).astype(np.uint64)
     assert np.array_equal(h.numpy(), oracle_ws(key1, plain, touched))
 
