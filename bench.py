@@ -378,6 +378,9 @@ def run_ours(args):
                "steps": es, "chunk_bytes": chunk, "streams": args.e2e_streams or 2,
                "host_memory": "pinned", "round_trip_ok": bool(ok),
                "link": link, "frac_of_link": round(e2e_gbs / world / link["bound_gbs"], 3)}
+        # the same passes in place over the host link (ms_crypt_host_inplace:
+        # the SMs read and write the pinned pages, no copy engine, no device buffer)
+        e2e["in_place"] = in_place_result(ms, ctx, hbuf, ne, es, head, link, world, d.device, barrier)
         del hbuf
 
     ctx.shutdown()
@@ -440,7 +443,8 @@ def run_ours(args):
                                    args.serve_seconds, one_per_launch_cap=args.one_per_launch_cap,
                                    reps_below=(1e5, args.low_rate_reps))
         keep = ("offered_pages_per_s", "mode", "requests", "arrival_s", "sustained_pages_per_s", "p50_us", "p99_us",
-                "p999_us", "reps", "p99_us_each", "first_second", "steady", "p99_us_by_second", "max_submit_lag_ms")
+                "p999_us", "reps", "p99_us_each", "first_second", "steady", "p99_us_by_second", "max_submit_lag_ms",
+                "max_server_pass_ms")
         one = {r["offered_pages_per_s"]: r for r in rows if r["mode"] == "one_per_launch"}
 
         def p99(r):  # the steady state where the run has one, else the whole run
@@ -749,6 +753,33 @@ def host_link(hbuf, probe=1 << 30, reps=5):
             "note": "the path moves every page both ways, so its bound is the slower direction while both run"}
 
 
+def in_place_result(ms, ctx, hbuf, n, steps, head, link, world=1, device=None, barrier=lambda: None):
+    """ms_crypt_host_inplace over the whole buffer: `steps` encrypt + decrypt
+    passes, host wall time from the first call to the final sync (max over
+    ranks when `device` is given)."""
+    ctx.crypt_host_inplace(ms.MS_ENCRYPT, hbuf, 0, n)
+    ctx.crypt_host_inplace(ms.MS_DECRYPT, hbuf, 0, n)
+    ctx.sync_checked()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.crypt_host_inplace(ms.MS_ENCRYPT, hbuf, 0, n)
+        ctx.crypt_host_inplace(ms.MS_DECRYPT, hbuf, 0, n)
+    ctx.sync_checked()
+    barrier()
+    el_ms = (time.perf_counter() - t0) * 1e3
+    if device is not None:
+        el_ms, gbs = aggregate_replicas(el_ms, 2.0 * steps * n * PAGE, world, device)
+    else:
+        gbs = 2.0 * steps * n * PAGE / (el_ms * 1e-3) / 1e9
+    import torch
+    return {"value": round(gbs, 3), "unit": "GB/s", "entry": "ms_crypt_host_inplace", "steps": steps,
+            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+            "link_bytes_per_step_each_way": 2 * n * PAGE,
+            "round_trip_ok": bool(torch.equal(hbuf[:PAGE * 64], head)),
+            "frac_of_link": round(gbs / world / link["bound_gbs"], 3)}
+
+
 def host_result(args, chunks_mib):
     """The host-page workload through ms_crypt_host at each chunk size, against
     the measured host link."""
@@ -777,6 +808,7 @@ def host_result(args, chunks_mib):
             rows.append({"chunk_mib": mib, "streams": ns, "gb_per_s": round(n * PAGE / el / 1e9, 2),
                          "frac_of_link": round(n * PAGE / el / 1e9 / link_bound, 3)})
     ok = torch.equal(hbuf[:PAGE * 64], head)
+    in_place = in_place_result(ms, ctx, hbuf, n, 3, head, link)
     ctx.shutdown()
     best = max(rows, key=lambda r: r["gb_per_s"])
     return {
@@ -785,7 +817,7 @@ def host_result(args, chunks_mib):
         "config": {"workload": "host pages: 4 GiB pinned host buffer (1,048,576 pages, seed 4), ms_crypt_host, "
                                "chunks 2..64 MiB, 2..4 streams", "pages": n},
         "link": link, "frac_of_link": round(best["gb_per_s"] / link_bound, 3), "sweep": rows,
-        "round_trip_ok": ok,
+        "round_trip_ok": ok, "in_place": in_place,
     }
 
 
@@ -946,6 +978,8 @@ def serve_rows(args, rates, modes, seconds, one_per_launch_cap=None, reps_below=
                         st = srv.stats()
                         for k in ("waves", "conflict_waits", "budget_waits", "gather_ns", "scatter_ns"):
                             st[k] -= st0[k]
+                        st["submit_lag_ms"] = round(st["replay_max_lag_ns"] * 1e-6, 3)
+                        st["server_pass_ms"] = round(st["max_pass_ns"] * 1e-6, 3)
                 multi = name == "resident" and args.resident_submitters > 1
                 total = st["waves"] if multi else int(offsets[-1])
                 us = lat * 1e6
@@ -981,6 +1015,8 @@ def serve_rows(args, rates, modes, seconds, one_per_launch_cap=None, reps_below=
                          "p99_us_each": [round(r["p99_us"], 1) for r in reps],
                          "p99_us_by_second": [r["by_sec"] for r in reps],
                          "max_submit_lag_ms": [r["st"].get("submit_lag_ms") for r in reps],
+                         "late_submissions": [r["st"].get("replay_late") for r in reps],
+                         "max_server_pass_ms": [r["st"].get("server_pass_ms") for r in reps],
                          "waves": st["waves"], "max_wave_requests": st["max_wave_requests"],
                          "conflict_waits": st["conflict_waits"], "budget_waits": st["budget_waits"],
                          "gather_s": round(st["gather_ns"] * 1e-9, 3), "scatter_s": round(st["scatter_ns"] * 1e-9, 3)})

@@ -40,7 +40,7 @@
  *   one launch          ms_encrypt_pages / ms_decrypt_pages (host list),
  *                       *_dev (device list), ms_crypt_pages_dom*, ms_crypt_range
  *   tickets             ms_submit_host, ms_poll, ms_wait
- *   host streaming      ms_crypt_host
+ *   host streaming      ms_crypt_host (copy engines), ms_crypt_host_inplace (in place over the link)
  *   shape and tuning    ms_get_shape / ms_set_shape, ms_autotune, ms_tune_save/load
  *   batched             ms_batch_* (persistent kernel, device queue, CUDA graphs)
  *   served              ms_server_* (continuous batching over a host working set)
@@ -299,6 +299,21 @@ int ms_crypt_host(ms_ctx *ctx, int op, void *host_base, uint64_t first_page_id, 
                   size_t chunk_bytes, int n_streams);
 
 /*
+ * Host pages, in place (Sec. 4.4's page transform applied where the page
+ * lies; the paper instead copies each page into GPU memory and back).
+ * n_pages (< 2^32) pages back to back at host_base, which must be pinned,
+ * mapped host memory (cudaHostAlloc, or registered and mapped), 16-byte
+ * aligned; page k has id first_page_id + k.  The kernel reads and writes the
+ * pages over the host link with a bounded grid (16 CTAs of 512 threads, each
+ * thread loading its next keystream block's bytes while it computes the
+ * current one) -- no device buffer, no copy engine.  Asynchronous on the
+ * context's stream like ms_crypt_range: the results are in host memory once
+ * ms_sync returns.  MS_EINVAL for memory that is not pinned and mapped, a
+ * misaligned base, or ids that would wrap past 2^64 - 1.
+ */
+int ms_crypt_host_inplace(ms_ctx *ctx, int op, void *host_base, uint64_t first_page_id, size_t n_pages);
+
+/*
  * ---- Batched form (persistent kernel fed by a device work queue) ----
  *
  * Sec. 4.4: the GPU module's workers take pages from queues that many host
@@ -468,6 +483,11 @@ typedef struct ms_server_stats {
   uint64_t scatter_ns;       /* ... and back into the working set */
   uint64_t inplace_waves;    /* waves run through the in-place lane (included in waves) */
   uint64_t staged_waves;     /* waves whose pages were copied through staging (included in waves) */
+  uint64_t max_pass_ns;      /* longest single pass of the server thread's loop (completions,
+                                admission, issue), its idle waits excluded; since the latest
+                                ms_server_replay started (else since creation) */
+  uint64_t replay_max_lag_ns;/* latest ms_server_replay: most a submission ran behind its schedule */
+  uint64_t replay_late;      /* ... and how many submissions ran more than 1 ms behind */
 } ms_server_stats;
 
 void ms_server_config_default(ms_server_config *cfg);

@@ -12,8 +12,13 @@
 //     next block while it computes the current one: about 32 GB/s each way;
 //   - without that prefetch the same grid stays near 8 GB/s, and from about
 //     48 CTAs x 512 threads up the rate falls back to 8 GB/s.
-// So this kernel runs at most kLinkCtas CTAs, whatever the number of pages,
-// and keeps two blocks per thread in flight.
+// And the access pattern matters once the concurrency is right: a thread
+// reading its own 64-byte block as 4 x 16 bytes (a warp instruction touching
+// 32 separate 16-byte pieces) fell to 8 GB/s on pages in random order over
+// 1 GiB, where warp instructions of 512 contiguous bytes moved 42 GB/s at any
+// grid of 8 to 32 CTAs x 512 threads.  So this kernel runs at most
+// kLinkCtas CTAs, whatever the number of pages, moves whole 512-byte rows
+// per warp instruction, and keeps the next step's bytes in flight.
 #include <algorithm>
 
 #include "ms_internal.h"
@@ -38,6 +43,20 @@ struct DevEntries {
   __device__ __forceinline__ ms_page_dom get(uint32_t i) const { return e[i]; }
 };
 
+// Pages back to back from `base` (device view), ids first_id + i.
+struct RangeEntries {
+  LinkHead h;
+  uint64_t base, first_id;
+  uint32_t domain;
+  __device__ __forceinline__ ms_page_dom get(uint32_t i) const {
+    ms_page_dom e{};
+    e.addr = base + (uint64_t)i * MS_PAGE_BYTES;
+    e.page_id = first_id + i;
+    e.domain = domain;
+    return e;
+  }
+};
+
 // Entries in the kernel parameters (a short host list: no staging copy).
 template <int CAP>
 struct ParamEntries {
@@ -46,12 +65,12 @@ struct ParamEntries {
   __device__ __forceinline__ ms_page_dom get(uint32_t i) const { return e[i]; }
 };
 
-// The keystream block `counter` XORed into the 64 bytes `d` already loaded
-// from dst, then stored back.  The same block function as xor_block in the
-// cipher header, minus the loads (they were issued one step earlier).
+// The keystream block `counter` XORed into the 64 bytes `d` (in registers).
+// The same block function as xor_block in the cipher header, without its
+// loads and stores: here those go through the warp's transpose below.
 template <int ROUNDS>
-__device__ __forceinline__ void xor_loaded(uint4 *__restrict__ dst, uint4 (&d)[4], const BlockSeed &s,
-                                           uint32_t counter, const MulConsts &mc) {
+__device__ __forceinline__ void xor_keystream(uint4 (&d)[4], const BlockSeed &s, uint32_t counter,
+                                              const MulConsts &mc) {
   uint32_t x0 = kSigma0, x1 = kSigma1, x2 = kSigma2, x3 = kSigma3;
   uint32_t x4 = s.k[0], x5 = s.k[1], x6 = s.k[2], x7 = s.k[3];
   uint32_t x8 = s.k[4], x9 = s.k[5], x10 = s.k[6], x11 = s.k[7];
@@ -71,45 +90,90 @@ __device__ __forceinline__ void xor_loaded(uint4 *__restrict__ dst, uint4 (&d)[4
   d[1].x ^= x4 + s.k[0];   d[1].y ^= x5 + s.k[1];   d[1].z ^= x6 + s.k[2];   d[1].w ^= x7 + s.k[3];
   d[2].x ^= x8 + s.k[4];   d[2].y ^= x9 + s.k[5];   d[2].z ^= x10 + s.k[6];  d[2].w ^= x11 + s.k[7];
   d[3].x ^= x12 + counter; d[3].y ^= x13 + s.n0;    d[3].z ^= x14 + s.n1;    d[3].w ^= x15 + s.n2;
-  __stcs(dst + 0, d[0]); __stcs(dst + 1, d[1]); __stcs(dst + 2, d[2]); __stcs(dst + 3, d[3]);
 }
 
-__device__ __forceinline__ void load_unit(uint4 (&d)[4], uint64_t addr, uint32_t t) {
-  const uint4 *p = reinterpret_cast<const uint4 *>(addr) + 4 * t;
-  d[0] = __ldcs(p); d[1] = __ldcs(p + 1); d[2] = __ldcs(p + 2); d[3] = __ldcs(p + 3);
+// A warp works on 32 consecutive keystream blocks (2 KiB) of one page per
+// step.  It moves them over the host link as 4 loads (and 4 stores) of 512
+// contiguous bytes -- lane l takes 16-byte slot 32 k + l of the span -- and
+// swaps them through 2 KiB of shared memory so that lane l holds block l
+// (slots 4 l .. 4 l + 3).  Slot i is kept at i ^ ((i >> 3) & 3), which makes
+// both the row pattern (32 k + l) and the block pattern (4 l + j) free of
+// bank conflicts (each quarter-warp phase touches 8 distinct 16-byte banks).
+__device__ __forceinline__ uint32_t swz(uint32_t i) { return i ^ ((i >> 3) & 3u); }
+
+__device__ __forceinline__ uint4 *span_of(uint64_t addr, uint64_t u) {
+  return reinterpret_cast<uint4 *>(addr) + ((u % 64) & ~31ull) * 4;
+}
+
+__device__ __forceinline__ void load_span(uint4 (&row)[4], const uint4 *span, uint32_t lane) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) row[k] = __ldcs(span + 32 * k + lane);
+}
+
+__device__ __forceinline__ void rows_to_block(uint4 *sb, const uint4 (&row)[4], uint4 (&blk)[4], uint32_t lane) {
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sb[swz(32 * k + lane)] = row[k];
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) blk[j] = sb[swz(4 * lane + j)];
+}
+
+__device__ __forceinline__ void store_block(uint4 *sb, const uint4 (&blk)[4], uint4 *span, uint32_t lane) {
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sb[swz(4 * lane + j)] = blk[j];
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) __stcs(span + 32 * k + lane, sb[swz(32 * k + lane)]);
 }
 
 // Unit u = (page u / 64, block u % 64); thread g takes units g, g + stride,
-// ..., so at each step the 32 lanes of a warp work on 32 consecutive blocks
-// (2 KiB) of one page.
+// ...  Units per page (64) and the stride are multiples of 32, so the 32
+// lanes of a warp always hold 32 consecutive blocks of one page and take
+// every branch below together.  The next step's span is loaded while the
+// current step's blocks are computed.
 template <int ROUNDS, typename Src>
 __global__ void __launch_bounds__(kLinkThreads) k_pages_link(const __grid_constant__ Src src) {
+  __shared__ uint4 sbuf[kLinkThreads / 32][128];
   const uint64_t units = (uint64_t)src.h.n_pages * 64;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= units) return;
+  const uint32_t lane = threadIdx.x & 31u;
+  uint4 *sb = sbuf[threadIdx.x >> 5];
   BlockSeed s;
   load_key(src.h.key, s.k);
   ms_page_dom e = src.get((uint32_t)(u / 64));
   bool ok = entry_ok(e.addr);
-  uint4 cur[4] = {};
-  if (ok) load_unit(cur, e.addr, (uint32_t)(u % 64));
+  uint4 *span = ok ? span_of(e.addr, u) : nullptr;
+  uint4 blk[4] = {};
+  if (ok) {
+    uint4 row[4];
+    load_span(row, span, lane);
+    rows_to_block(sb, row, blk, lane);
+  }
   for (;;) {
     const uint64_t un = u + stride;
     ms_page_dom en{};
     bool okn = false;
-    uint4 nxt[4] = {};
-    if (un < units) {  // the next unit's bytes are in flight while this one is computed
+    uint4 *spann = nullptr;
+    uint4 nrow[4] = {};
+    if (un < units) {  // the next span is in flight while this one is computed
       en = src.get((uint32_t)(un / 64));
       okn = entry_ok(en.addr);
-      if (okn) load_unit(nxt, en.addr, (uint32_t)(un % 64));
+      if (okn) {
+        spann = span_of(en.addr, un);
+        load_span(nrow, spann, lane);
+      }
     }
     const uint32_t t = (uint32_t)(u % 64);
     if (ok) {
       s.n0 = (uint32_t)e.page_id;
       s.n1 = (uint32_t)(e.page_id >> 32);
       s.n2 = e.domain;
-      xor_loaded<ROUNDS>(reinterpret_cast<uint4 *>(e.addr) + 4 * t, cur, s, t, src.h.mc);
+      xor_keystream<ROUNDS>(blk, s, t, src.h.mc);
+      store_block(sb, blk, span, lane);
     } else if (t == 0) {
       atomicOr(src.h.status, kStatusBadEntry);
     }
@@ -117,7 +181,8 @@ __global__ void __launch_bounds__(kLinkThreads) k_pages_link(const __grid_consta
     u = un;
     e = en;
     ok = okn;
-    cur[0] = nxt[0]; cur[1] = nxt[1]; cur[2] = nxt[2]; cur[3] = nxt[3];
+    span = spann;
+    if (ok) rows_to_block(sb, nrow, blk, lane);
   }
 }
 
@@ -183,3 +248,32 @@ cudaError_t launch_pages_link_dev(const ms_ctx *c, const ms_page_dom *d_pages, s
 }
 
 }  // namespace ms
+
+using namespace ms;
+
+extern "C" int ms_crypt_host_inplace(ms_ctx *c, int op, void *host_base, uint64_t first_page_id,
+                                     size_t n_pages) {
+  if (!c || !c->alive) return MS_ENOTINIT;
+  if (op != MS_ENCRYPT && op != MS_DECRYPT) return MS_EINVAL;
+  if (n_pages == 0) return MS_OK;
+  if (!host_base || ((uintptr_t)host_base & 15u)) return MS_EINVAL;
+  if (n_pages - 1 > ~first_page_id) return MS_EINVAL;  // ids must not wrap past 2^64 - 1
+  if (n_pages > UINT32_MAX) return MS_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  void *dev = nullptr;
+  if (cudaHostGetDevicePointer(&dev, host_base, 0) != cudaSuccess || !dev) {
+    cudaGetLastError();
+    return MS_EINVAL;  // not pinned, mapped host memory
+  }
+  cudaError_t e = injected(MS_FAULT_LAUNCH);
+  if (e == cudaSuccess) {
+    RangeEntries r;
+    r.h = make_head(c, n_pages);
+    r.base = (uint64_t)dev;
+    r.first_id = first_page_id;
+    r.domain = c->cfg.domain;
+    e = launch_src(c, r, n_pages, c->stream);
+  }
+  return e == cudaSuccess ? MS_OK : cuda_fail(c, e);
+}

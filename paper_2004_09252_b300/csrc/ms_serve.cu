@@ -187,9 +187,16 @@ struct ms_server {
   cudaStream_t s_link = nullptr;
   uint32_t inplace_max = 0;       // pages of an in-place wave at most (0: lane off)
   std::vector<Req> reqs;
+  // Submitters hold inmu only to claim a request slot and append its ticket
+  // to the inbox; the server thread moves the inbox into `incoming` (its
+  // own queue) at each pass.  So forming and completing waves, however long
+  // under load, never hold up a submission.
+  std::mutex inmu;
+  std::condition_variable qcv;       // with inmu: wakes an idle server thread
+  std::vector<uint64_t> inbox;       // submitted tickets, in submission order (guarded by inmu)
+  std::vector<uint64_t> inbox_spare; // the server thread's swap buffer for the inbox
   std::mutex qmu;
-  std::condition_variable qcv;
-  std::deque<uint64_t> incoming;
+  std::deque<uint64_t> incoming;     // server thread only
   std::atomic<uint64_t> next_ticket{0};
   ms::Admission *adm = nullptr;  // staging ring and in-flight pages (guarded by qmu)
   std::deque<Wave> inflight;
@@ -204,12 +211,14 @@ struct ms_server {
   std::mutex done_mu;
   std::condition_variable done_cv;
   std::atomic<uint64_t> st_req{0}, st_pages{0}, st_waves{0}, st_maxreq{0}, st_maxpages{0}, st_conflict{0},
-      st_budget{0}, st_maxstaged{0}, st_gather_ns{0}, st_scatter_ns{0}, st_inplace{0}, st_staged{0};
+      st_budget{0}, st_maxstaged{0}, st_gather_ns{0}, st_scatter_ns{0}, st_inplace{0}, st_staged{0}, st_max_pass{0},
+      st_replay_lag{0}, st_replay_late{0};
   uint64_t d_host = 0;  // device address of host_base (zero-copy mode)
   uint64_t idle_spin_ns = 0;
 
   Req &slot(uint64_t t) { return reqs[t % reqs.size()]; }
   void loop();
+  void take_inbox();
   bool form_wave(Wave &w);
   bool form_inplace(Wave &w, uint32_t max_pages);
   int issue(Wave &w);
@@ -232,6 +241,16 @@ void atomic_max(std::atomic<uint64_t> &a, uint64_t v) {
 // Admission (see ms_admission.h): at most kScanWindow queued requests are
 // considered per wave.
 constexpr size_t kScanWindow = 4096;
+
+void ms_server::take_inbox() {
+  {
+    std::lock_guard<std::mutex> lk(inmu);
+    if (inbox.empty()) return;
+    inbox.swap(inbox_spare);  // the inbox keeps the spare's (empty) buffer
+  }
+  incoming.insert(incoming.end(), inbox_spare.begin(), inbox_spare.end());
+  inbox_spare.clear();
+}
 
 bool ms_server::form_wave(Wave &w) {
   std::lock_guard<std::mutex> lk(qmu);
@@ -404,6 +423,7 @@ void ms_server::complete(Wave &w) {
 
 void ms_server::fail_all(int code) {
   error.store(code);
+  take_inbox();  // a submission that saw no error under inmu is in the inbox by now
   std::lock_guard<std::mutex> lk(qmu);
   for (auto *set : {&inflight, &inflight_inplace})
     for (Wave &w : *set)
@@ -430,6 +450,7 @@ void ms_server::loop() {
   uint64_t idle_since = 0;
   for (;;) {
     bool progress = false;
+    const uint64_t t_pass = now_ns();
     while (!inflight.empty()) {
       cudaError_t q = cudaEventQuery(inflight.front().ev_done);
       if (q == cudaErrorNotReady) break;
@@ -459,12 +480,9 @@ void ms_server::loop() {
       it = inflight_inplace.erase(it);
       progress = true;
     }
+    take_inbox();
     if (stop.load()) {
-      bool empty;
-      {
-        std::lock_guard<std::mutex> lk(qmu);
-        empty = incoming.empty();
-      }
+      const bool empty = incoming.empty();
       if (empty && inflight.empty() && inflight_inplace.empty()) break;
       if (!stop_deadline) stop_deadline = now_ns() + (uint64_t)ctx->cfg.timeout_ms * 1000000ull;
       if (now_ns() > stop_deadline) {
@@ -508,6 +526,7 @@ void ms_server::loop() {
         progress = true;
       }
     }
+    atomic_max(st_max_pass, now_ns() - t_pass);  // this pass's work, without its idle waits
     if (progress) {
       idle_since = 0;
       continue;
@@ -518,8 +537,8 @@ void ms_server::loop() {
       const uint64_t seen = next_ticket.load(), t_idle = now_ns();
       while (next_ticket.load() == seen && !stop.load() && now_ns() - t_idle < idle_spin_ns) nap_ns(1000);
       if (next_ticket.load() == seen && !stop.load()) {
-        std::unique_lock<std::mutex> lk(qmu);
-        qcv.wait_for(lk, std::chrono::milliseconds(1), [&] { return !incoming.empty() || stop.load(); });
+        std::unique_lock<std::mutex> lk(inmu);
+        qcv.wait_for(lk, std::chrono::milliseconds(1), [&] { return !inbox.empty() || stop.load(); });
       }
     } else {
       // a wave is on the GPU: poll, spinning briefly before napping
@@ -639,23 +658,27 @@ int ms_server_create(ms_ctx *c, void *host_base, uint64_t n_pages, const ms_serv
   return MS_OK;
 }
 
+// `checked`: the request was validated already (a replay checks every
+// request before its first submission).
 static int submit_internal(ms_server *s, int op, uint32_t domain, const uint64_t *page_index, uint32_t n,
-                           uint64_t *ticket, uint64_t t_sched, double *lat_out) {
+                           uint64_t *ticket, uint64_t t_sched, double *lat_out, bool checked = false) {
   if (!s) return MS_EINVAL;
-  if (op != MS_ENCRYPT && op != MS_DECRYPT) return MS_EINVAL;
-  if (n == 0 || !page_index) return MS_EINVAL;
-  if (n > s->cfg.max_request_pages) return MS_ERANGE;
-  if (s->error.load()) return s->error.load();
-  if (s->stop.load()) return MS_ENOTINIT;
-  for (uint32_t i = 0; i < n; ++i)
-    if (page_index[i] >= s->n_pages) return MS_EINVAL;
-  // distinct pages within a request (two in-place updates of one page in one wave would race)
-  if (n > 1) {
-    std::vector<uint64_t> tmp(page_index, page_index + n);
-    std::sort(tmp.begin(), tmp.end());
-    if (std::adjacent_find(tmp.begin(), tmp.end()) != tmp.end()) return MS_EINVAL;
+  if (!checked) {
+    if (op != MS_ENCRYPT && op != MS_DECRYPT) return MS_EINVAL;
+    if (n == 0 || !page_index) return MS_EINVAL;
+    if (n > s->cfg.max_request_pages) return MS_ERANGE;
+    for (uint32_t i = 0; i < n; ++i)
+      if (page_index[i] >= s->n_pages) return MS_EINVAL;
+    // distinct pages within a request (two in-place updates of one page in one wave would race)
+    if (n > 1) {
+      std::vector<uint64_t> tmp(page_index, page_index + n);
+      std::sort(tmp.begin(), tmp.end());
+      if (std::adjacent_find(tmp.begin(), tmp.end()) != tmp.end()) return MS_EINVAL;
+    }
   }
-  std::lock_guard<std::mutex> lk(s->qmu);
+  std::lock_guard<std::mutex> lk(s->inmu);
+  if (s->error.load()) return s->error.load();  // under inmu: fail_all drains the inbox after setting it
+  if (s->stop.load()) return MS_ENOTINIT;
   const uint64_t t = s->next_ticket.load();
   Req &r = s->slot(t);
   int st = r.state.load();
@@ -671,7 +694,7 @@ static int submit_internal(ms_server *s, int op, uint32_t domain, const uint64_t
   r.t_sched_ns = t_sched ? t_sched : now_ns();
   r.lat_out = lat_out;
   r.state.store(kQueued, std::memory_order_release);
-  s->incoming.push_back(t);
+  s->inbox.push_back(t);
   if (ticket) *ticket = t;
   s->qcv.notify_one();
   return MS_OK;
@@ -746,6 +769,8 @@ int ms_server_replay(ms_server *s, size_t n, const double *arrival_s, const int 
     }
   } restore{old_slack};
   const uint64_t t0 = now_ns() + 1000000ull;  // start 1 ms from now
+  uint64_t max_lag = 0, late = 0;  // how far submissions ran behind their schedule
+  s->st_max_pass.store(0);         // the longest server pass is reported per replay
   std::vector<uint64_t> tickets(n);
   size_t issued = 0;
   // On an early return the requests still queued or running must stop
@@ -773,9 +798,12 @@ int ms_server_replay(ms_server *s, size_t n, const double *arrival_s, const int 
     for (;;) {
       const uint32_t dom = domains ? domains[r] : s->ctx->cfg.domain;
       int rc = submit_internal(s, ops[r], dom, page_index + offsets[r], (uint32_t)n_pg, &tickets[r], target,
-                               &latency_s[r]);
+                               &latency_s[r], true);
       if (rc == MS_OK) {
         issued = r + 1;
+        const uint64_t lag = now_ns() - target;
+        max_lag = std::max(max_lag, lag);
+        late += lag > 1000000ull;
         break;
       }
       if (rc != MS_EBUSY) return detach(rc);
@@ -783,6 +811,8 @@ int ms_server_replay(ms_server *s, size_t n, const double *arrival_s, const int 
       nap_ns(5000);
     }
   }
+  s->st_replay_lag.store(max_lag);
+  s->st_replay_late.store(late);
   const uint64_t deadline = now_ns() + (uint64_t)timeout_ms * 1000000ull;
   uint64_t last = t0;
   for (size_t r = 0; r < n; ++r) {
@@ -816,6 +846,9 @@ int ms_server_get_stats(const ms_server *s, ms_server_stats *out) {
   out->scatter_ns = s->st_scatter_ns.load();
   out->inplace_waves = s->st_inplace.load();
   out->staged_waves = s->st_staged.load();
+  out->max_pass_ns = s->st_max_pass.load();
+  out->replay_max_lag_ns = s->st_replay_lag.load();
+  out->replay_late = s->st_replay_late.load();
   return MS_OK;
 }
 

@@ -112,7 +112,8 @@ class ms_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("requests_done", "pages_done", "waves", "max_wave_requests",
                                                "max_wave_pages", "conflict_waits", "budget_waits",
                                                "max_staged_pages", "gather_ns", "scatter_ns", "inplace_waves",
-                                               "staged_waves")]
+                                               "staged_waves", "max_pass_ns", "replay_max_lag_ns",
+                                               "replay_late")]
 
 
 MS_SERVE_CONTINUOUS, MS_SERVE_ONE_PER_LAUNCH, MS_SERVE_ZERO_COPY = 0, 1, 2
@@ -187,6 +188,7 @@ def _load():
         "ms_last_cuda_error": (I, [P]),
         "ms_debug_inject_fault": (I, [I, I, I]),
         "ms_crypt_host": (I, [P, I, P, U64, S, S, I]),
+        "ms_crypt_host_inplace": (I, [P, I, P, U64, S]),
         "ms_get_shape": (I, [P, ctypes.POINTER(ms_shape)]),
         "ms_set_shape": (I, [P, ctypes.POINTER(ms_shape)]),
         "ms_crypt_pages_noalloc": (I, [P, I, P, S]),
@@ -390,6 +392,11 @@ class Context:
                    n_streams: int = 0) -> None:
         _check(_lib.ms_crypt_host(self.handle, op, _ptr(host_base), first_page_id, n_pages, chunk_bytes,
                                   n_streams), "ms_crypt_host")
+
+    def crypt_host_inplace(self, op: int, host_base, first_page_id: int, n_pages: int) -> None:
+        """In place on pinned, mapped host pages over the host link (asynchronous; sync waits)."""
+        _check(_lib.ms_crypt_host_inplace(self.handle, op, _ptr(host_base), first_page_id, n_pages),
+               "ms_crypt_host_inplace")
 
     def crypt_pages_noalloc(self, op: int, pages: np.ndarray) -> None:
         """Same transform as encrypt_pages, with no allocation in the call (waits for completion)."""

@@ -41,6 +41,9 @@ def test_default_line_keys():
     assert e["unit"] == "GB/s" and e["value"] > 0 and e["round_trip_ok"] is True
     assert e["h2d_bytes_per_step"] == e["d2h_bytes_per_step"] == 2 * 65536 * 4096
     assert e["link"]["bound_gbs"] > 0 and 0 < e["frac_of_link"]
+    ip = e["in_place"]                               # the same passes in place over the host link
+    assert ip["value"] > 0 and ip["round_trip_ok"] is True and ip["h2d_bytes_per_step"] == 0
+    assert ip["link_bytes_per_step_each_way"] == 2 * 65536 * 4096
     c = d["cpu_baseline"]
     assert c["kind"] == "oracle" and c["cores"] >= 1 and c["value"] > 0 and c["sample"]
     assert set(d["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}

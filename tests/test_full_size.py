@@ -1,5 +1,6 @@
-"""Parity at the full sizes of the host-streaming (4 GiB pinned host buffer)
-and serving (16 GiB pinned working set) configurations, each compared whole
+"""Parity at the full sizes of the host configuration (4 GiB pinned host
+buffer, streamed through the copy engines and in place over the link) and
+serving (16 GiB pinned working set) configurations, each compared whole
 with the oracle, in the launch configurations the benchmark uses."""
 import numpy as np
 import pytest
@@ -38,6 +39,29 @@ def test_host_config_4gib(ms, key1):
         assert np.array_equal(h.numpy(), want)
         ctx.crypt_host(ms.MS_DECRYPT, h, 0, n, 16 << 20, 2)
     oracle.crypt_pages(key1, want, ids, ids, threads=threads)  # the same XOR again: the input
+    assert np.array_equal(h.numpy(), want)
+
+
+def test_host_config_4gib_in_place(ms, key1):
+    """The same 4 GiB buffer encrypted in place over the host link
+    (ms_crypt_host_inplace, the bounded-grid kernel): the whole result
+    against the oracle, then decrypted back to the input."""
+    import os
+    n = 1048576
+    h = torch.empty(n * PAGE, dtype=torch.uint8).pin_memory()
+    synth.fill_pages(h.data_ptr(), 4, 0, n)
+    want = np.empty(n * PAGE, dtype=np.uint8)
+    synth.fill_pages(want.ctypes.data, 4, 0, n)
+    ids = np.arange(n, dtype=np.uint64)
+    threads = max(1, os.cpu_count() or 1)
+    with ms.Context(key1) as ctx:
+        ctx.crypt_host_inplace(ms.MS_ENCRYPT, h, 0, n)
+        ctx.sync_checked()
+        oracle.crypt_pages(key1, want, ids, ids, threads=threads)
+        assert np.array_equal(h.numpy(), want)
+        ctx.crypt_host_inplace(ms.MS_DECRYPT, h, 0, n)
+        ctx.sync_checked()
+    oracle.crypt_pages(key1, want, ids, ids, threads=threads)
     assert np.array_equal(h.numpy(), want)
 
 
