@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "ms_internal.h"
+#include "ms_link.cuh"
 
 namespace {
 
@@ -97,6 +98,7 @@ __device__ __forceinline__ void st_release_sys32(uint32_t *p, uint32_t v) {
 __global__ void __launch_bounds__(kWorkerThreads) k_resident(const ResidentArgs a) {
   __shared__ RingEntry s_e[kPagesPerPass];
   __shared__ int s_n;
+  __shared__ uint4 s_rows[kWorkerThreads / 32][128];  // each warp's 2 KiB row transpose
   const uint32_t tid = threadIdx.x;
   const uint32_t lane = tid % 32;
   uint64_t i = a.sh->next;  // written by the previous launch / the host before this launch
@@ -169,6 +171,8 @@ __global__ void __launch_bounds__(kWorkerThreads) k_resident(const ResidentArgs 
     const int n = s_n;
     if (n < 0) return;
     if (n > 0) {
+      // page `slot` of the pass; warp 2 slot + h takes its blocks 32 h .. 32 h + 31
+      // as 512-byte rows over the host link (the branch is warp-uniform)
       const uint32_t slot = tid / 64, t = tid % 64;
       if (slot < (uint32_t)n) {
         const RingEntry e = s_e[slot];
@@ -176,7 +180,12 @@ __global__ void __launch_bounds__(kWorkerThreads) k_resident(const ResidentArgs 
           s.n0 = (uint32_t)e.page_id;
           s.n1 = (uint32_t)(e.page_id >> 32);
           s.n2 = e.domain;
-          ms::xor_block<20, 10, ms::kRotPerm>(reinterpret_cast<uint4 *>(e.addr) + 4 * t, s, t, a.mc);
+          uint4 *span = ms::span_of(e.addr, t);
+          uint4 row[4], blk[4];
+          ms::load_span(row, span, lane);
+          ms::rows_to_block(s_rows[tid / 32], row, blk, lane);
+          ms::xor_keystream<20>(blk, s, t, a.mc);
+          ms::store_block(s_rows[tid / 32], blk, span, lane);
         }
       }
       __threadfence_system();  // this thread's page writes are visible before the done word
