@@ -809,6 +809,18 @@ def host_result(args, chunks_mib):
                          "frac_of_link": round(n * PAGE / el / 1e9 / link_bound, 3)})
     ok = torch.equal(hbuf[:PAGE * 64], head)
     in_place = in_place_result(ms, ctx, hbuf, n, 3, head, link)
+    # the one-launch page kernel on the same pinned pages through their device
+    # view (ms_crypt_range): a grid of one thread per 4 keystream blocks, the
+    # shape that suits HBM, against the bounded grid of ms_crypt_host_inplace
+    dev = ms.host_device_address(hbuf)
+    t0 = time.perf_counter()
+    ctx.crypt_range(ms.MS_ENCRYPT, dev, 0, n)
+    ctx.crypt_range(ms.MS_DECRYPT, dev, 0, n)
+    ctx.sync_checked()
+    el = time.perf_counter() - t0
+    in_place["full_grid_one_launch"] = {"value": round(2 * n * PAGE / el / 1e9, 3), "unit": "GB/s",
+                                        "entry": "ms_crypt_range on the device view",
+                                        "round_trip_ok": bool(torch.equal(hbuf[:PAGE * 64], head))}
     ctx.shutdown()
     best = max(rows, key=lambda r: r["gb_per_s"])
     return {
@@ -1233,7 +1245,7 @@ def main():
     ap.add_argument("--window-free", type=int, default=1,
                     help="background eviction threshold: free window slots the evictor keeps")
     ap.add_argument("--window-backends", type=lambda v: v.split(","), default=["server", "resident", "ticketed"],
-                    help="serve the window clients through the staged server, resident workers and/or "
+                    help="serve the window clients through the continuous server, resident workers and/or "
                          "ticketed launches")
     ap.add_argument("--waves-in-flight", type=int, default=0, help="serving pipeline depth (0 = library default)")
     ap.add_argument("--max-wave-pages", type=int, default=0, help="serving wave size cap (0 = library default)")
