@@ -145,6 +145,35 @@ def test_replay_full_rings(ms, key1, workers, ring):
     assert np.array_equal(h.numpy(), want)
 
 
+def test_concurrent_submitters(ms, key1):
+    """Four threads submit single pages at once (disjoint pages: a page is not
+    resubmitted while pending) and wait for their own tickets; every worker
+    ring is shared by all four threads.  The result matches the oracle."""
+    import threading
+    n, per = 2048, 400
+    plain = synth.page_bytes_fast(121, 0, n)
+    h = torch.from_numpy(plain.copy()).pin_memory()
+    slots = synth.scattered_slots(122, n, 4 * per).astype(np.uint64)
+    errors = []
+    with ms.Context(key1) as ctx, ms.Resident(ctx, workers=4, ring_entries=64) as res:
+        def client(mine):
+            try:
+                ts = submit_all(res, h.data_ptr() + PAGE * mine, mine, np.zeros(len(mine), np.uint32))
+                for t in ts:
+                    res.wait(t)
+            except Exception as e:  # noqa: BLE001  (reported below)
+                errors.append(e)
+        threads = [threading.Thread(target=client, args=(slots[i * per:(i + 1) * per],)) for i in range(4)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        st = res.stats()
+    assert not errors, errors
+    assert st["requests"] == 4 * per
+    assert np.array_equal(h.numpy(), expected(key1, plain, slots, slots, np.zeros(4 * per, np.uint32)))
+
+
 def test_config_checks(ms, key1):
     with ms.Context(key1, rounds=12) as ctx:
         with pytest.raises(ms.MemShieldError):

@@ -140,6 +140,57 @@ def test_conflicting_requests_serialise(ms, key1):
     assert st["conflict_waits"] > 0
 
 
+@pytest.mark.parametrize("lane", [None, 0])
+def test_concurrent_submitters(ms, key1, lane):
+    """Four threads submit at once (each ctypes call releases the GIL) on
+    overlapping pages, waiting for some of their tickets as they go: the
+    inbox takes every request, admission serialises requests that share a
+    page, and the final state is the closed form of the application counts,
+    with the in-place waves and with every wave staged."""
+    import threading
+    n, per_thread, n_threads = 256, 300, 4
+    h = working_set(84, n)
+    plain = h.numpy().copy()
+    rng = synth.splitmix64(85, 0, n_threads * per_thread * 17)
+    reqs = []
+    for th in range(n_threads):
+        mine = []
+        for r in range(per_thread):
+            i = (th * per_thread + r) * 17
+            k = 1 + int(rng[i] % np.uint64(16))
+            sel = np.unique((rng[i + 1:i + 1 + k] % np.uint64(64)).astype(np.int64))
+            mine.append((r % 2, sel))
+        reqs.append(mine)
+    counts = np.zeros(n, dtype=np.int64)
+    for mine in reqs:
+        for _, sel in mine:
+            counts[sel] += 1
+    errors = []
+    with ms.Context(key1) as ctx, ms.Server(ctx, h, n, max_request_pages=16, zero_copy_max_pages=lane) as srv:
+        def client(mine):
+            try:
+                pending = []
+                for j, (op, sel) in enumerate(mine):
+                    pending.append(srv.submit(op, sel))
+                    if j % 7 == 6:
+                        srv.wait(pending.pop(0))
+                for t in pending:
+                    srv.wait(t)
+            except Exception as e:  # noqa: BLE001  (reported below)
+                errors.append(e)
+        threads = [threading.Thread(target=client, args=(m,)) for m in reqs]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        st = srv.stats()
+    assert not errors, errors
+    odd = np.nonzero(counts % 2)[0].astype(np.uint64)
+    assert np.array_equal(h.numpy(), oracle_ws(key1, plain, odd))
+    assert st["requests_done"] == n_threads * per_thread
+    assert (st["staged_waves"] == st["waves"]) if lane == 0 else (st["staged_waves"] == 0)
+
+
 def test_in_place_lane_with_conflicts(ms, key1):
     """Requests submitted a few at a time on overlapping pages, with the
     in-place lane on: short queues go through the lane, longer ones form
