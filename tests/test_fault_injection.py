@@ -67,6 +67,25 @@ def test_countdown_skips_earlier_calls(ms, key1):
     assert np.array_equal(d.cpu().numpy(), oracle_expected(key1, plain, ids, ids))
 
 
+def test_host_in_place_launch_failure(ms, key1):
+    """A failed launch of the host-link kernel (ms_crypt_host_inplace) leaves
+    the pinned pages untouched, reports the error, and the next call works."""
+    n = 300
+    plain = synth.page_bytes(123, 0, n)
+    h = torch.from_numpy(plain.copy()).pin_memory()
+    with ms.Context(key1) as ctx:
+        ms.inject_fault(ms.MS_FAULT_LAUNCH, 0, ERR)
+        with pytest.raises(ms.MemShieldError) as e:
+            ctx.crypt_host_inplace(ms.MS_ENCRYPT, h, 0, n)
+        assert e.value.code == ms.MS_ECUDA and ctx.last_cuda_error() == ERR
+        ctx.sync_checked()
+        assert np.array_equal(h.numpy(), plain)
+        ctx.crypt_host_inplace(ms.MS_ENCRYPT, h, 0, n)
+        ctx.sync_checked()
+    ids = np.arange(n, dtype=np.uint64)
+    assert np.array_equal(h.numpy(), oracle_expected(key1, plain, ids, ids))
+
+
 def test_host_stream_copy_failure(ms, key1):
     n = 600
     plain = synth.page_bytes(122, 0, n)
