@@ -30,6 +30,25 @@
 
 namespace ms {
 
+// Per-page marks, two bits a page: in flight (in an admitted, not yet
+// completed wave) and blocked (skipped earlier in the current scan).  As
+// bitsets the marks of a 16 GiB working set (4M pages) take 1 MiB, so the
+// scans of a large wave stay in cache (a byte a page took 4 MiB, and random
+// accesses to it cost the server thread milliseconds per large wave).
+class PageMarks {
+ public:
+  explicit PageMarks(uint64_t n) : busy_((n + 63) / 64, 0), blocked_((n + 63) / 64, 0) {}
+  bool taken(uint64_t pg) const { return ((busy_[pg >> 6] | blocked_[pg >> 6]) >> (pg & 63)) & 1u; }
+  void set_busy(uint64_t pg) { busy_[pg >> 6] |= bit(pg); }
+  void clear_busy(uint64_t pg) { busy_[pg >> 6] &= ~bit(pg); }
+  void set_blocked(uint64_t pg) { blocked_[pg >> 6] |= bit(pg); }
+  void clear_blocked(uint64_t pg) { blocked_[pg >> 6] &= ~bit(pg); }
+
+ private:
+  static uint64_t bit(uint64_t pg) { return 1ull << (pg & 63); }
+  std::vector<uint64_t> busy_, blocked_;
+};
+
 struct AdmittedWave {
   std::vector<uint64_t> tickets;
   uint32_t pos = 0;   // first staging slot
@@ -40,7 +59,7 @@ struct AdmittedWave {
 class Admission {
  public:
   Admission(uint32_t slots, uint32_t max_wave_pages, bool one_per_launch, uint64_t n_pages, size_t window)
-      : S_(slots), max_wave_(max_wave_pages), one_(one_per_launch), window_(window), busy_(n_pages, 0) {}
+      : S_(slots), max_wave_(max_wave_pages), one_(one_per_launch), window_(window), marks_(n_pages) {}
 
   uint32_t slots() const { return S_; }
   uint32_t used() const { return used_; }
@@ -73,21 +92,21 @@ class Admission {
       }
       bool conflict = false;
       for (uint64_t pg : pages)
-        if (busy_[pg]) {
+        if (marks_.taken(pg)) {
           conflict = true;
           break;
         }
       if (conflict) {
         ++conflict_waits;
         for (uint64_t pg : pages)
-          if (!busy_[pg]) {
-            busy_[pg] = 2;  // blocked for the rest of this scan
+          if (!marks_.taken(pg)) {
+            marks_.set_blocked(pg);  // blocked for the rest of this scan
             blocked.push_back(pg);
           }
         taken.push_back(0);
         continue;
       }
-      for (uint64_t pg : pages) busy_[pg] = 1;
+      for (uint64_t pg : pages) marks_.set_busy(pg);
       pos = p;
       waste = wst;
       len += n;
@@ -95,7 +114,7 @@ class Admission {
       taken.push_back(1);
       ++n_taken;
     }
-    for (uint64_t pg : blocked) busy_[pg] = 0;
+    for (uint64_t pg : blocked) marks_.clear_blocked(pg);
     if (n_taken == 0) return false;
     // drop the admitted tickets from the scanned prefix, keeping the skipped ones in order
     const size_t scanned = taken.size();
@@ -127,25 +146,25 @@ class Admission {
       const auto &pages = pages_of(t);
       bool conflict = false;
       for (uint64_t pg : pages)
-        if (busy_[pg]) {
+        if (marks_.taken(pg)) {
           conflict = true;
           break;
         }
       if (conflict) {
         ++conflict_waits;
         for (uint64_t pg : pages)
-          if (!busy_[pg]) {
-            busy_[pg] = 2;
+          if (!marks_.taken(pg)) {
+            marks_.set_blocked(pg);
             blocked.push_back(pg);
           }
         keep.push_back(t);
         continue;
       }
-      for (uint64_t pg : pages) busy_[pg] = 1;
+      for (uint64_t pg : pages) marks_.set_busy(pg);
       len += (uint32_t)pages.size();
       w.tickets.push_back(t);
     }
-    for (uint64_t pg : blocked) busy_[pg] = 0;
+    for (uint64_t pg : blocked) marks_.clear_blocked(pg);
     if (w.tickets.empty()) return false;
     queue.assign(keep.begin(), keep.end());
     w.pos = 0;
@@ -160,7 +179,7 @@ class Admission {
   template <typename PagesOf>
   void release(const AdmittedWave &w, PagesOf pages_of) {
     for (uint64_t t : w.tickets)
-      for (uint64_t pg : pages_of(t)) busy_[pg] = 0;
+      for (uint64_t pg : pages_of(t)) marks_.clear_busy(pg);
     used_ -= w.span;
   }
 
@@ -168,7 +187,7 @@ class Admission {
   uint32_t S_, max_wave_;
   bool one_;
   size_t window_;
-  std::vector<uint8_t> busy_;
+  PageMarks marks_;
   uint32_t head_ = 0, used_ = 0;
 };
 
