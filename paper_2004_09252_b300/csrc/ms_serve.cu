@@ -316,18 +316,6 @@ int ms_server::issue_inplace(Wave &w) {
 
 int ms_server::issue(Wave &w) {
   if (!take_events(w)) return cuda_fail(ctx, cudaGetLastError());
-  // slot index of every page of the wave, in order
-  std::vector<std::pair<uint64_t, uint32_t>> map;  // (working-set page, staging slot)
-  map.reserve(w.len);
-  uint32_t k = w.pos;
-  for (uint64_t t : w.tickets) {
-    Req &r = slot(t);
-    r.state.store(kAdmitted, std::memory_order_release);
-    for (uint64_t pg : r.pages) {
-      h_ent[k].domain = r.domain;
-      map.push_back({pg, k++});
-    }
-  }
   // Zero-copy mode, and continuous mode whenever its in-place lane is on (a
   // pinned, mapped working set): the kernel works on the working set itself,
   // on the link stream, and only the entries use the wave's staging slots
@@ -336,12 +324,30 @@ int ms_server::issue(Wave &w) {
   const bool zc = cfg.mode == MS_SERVE_ZERO_COPY || inplace_max != 0;
   w.zc = zc;
   const uint64_t tg = now_ns();
-  if (zc) {  // the kernel works on the working set itself, through the host link
-    for (const auto &m : map) {
-      h_ent[m.second].addr = d_host + m.first * MS_PAGE_BYTES;
-      h_ent[m.second].page_id = m.first;
+  uint32_t k = w.pos;
+  if (zc) {  // entries point at the working set: no per-page map, no copies
+    for (uint64_t t : w.tickets) {
+      Req &r = slot(t);
+      r.state.store(kAdmitted, std::memory_order_release);
+      for (uint64_t pg : r.pages) {
+        h_ent[k].addr = d_host + pg * MS_PAGE_BYTES;
+        h_ent[k].page_id = pg;
+        h_ent[k].domain = r.domain;
+        ++k;
+      }
     }
   } else {
+    // slot index of every page of the wave, in order
+    std::vector<std::pair<uint64_t, uint32_t>> map;  // (working-set page, staging slot)
+    map.reserve(w.len);
+    for (uint64_t t : w.tickets) {
+      Req &r = slot(t);
+      r.state.store(kAdmitted, std::memory_order_release);
+      for (uint64_t pg : r.pages) {
+        h_ent[k].domain = r.domain;
+        map.push_back({pg, k++});
+      }
+    }
     pool->run(map.size(), [&](size_t i) {
       const uint64_t pg = map[i].first;
       const uint32_t sl = map[i].second;
@@ -378,14 +384,14 @@ int ms_server::issue(Wave &w) {
 }
 
 void ms_server::complete(Wave &w) {
-  std::vector<std::pair<uint64_t, uint32_t>> map;
-  map.reserve(w.len);
-  uint32_t k = w.pos;
-  for (uint64_t t : w.tickets)
-    for (uint64_t pg : slot(t).pages) map.push_back({pg, k++});
   const bool wipe = cfg.zero_staging != 0;
   const uint64_t ts = now_ns();
-  if (!w.zc) {
+  if (!w.zc) {  // a staged wave: its pages go back into the working set
+    std::vector<std::pair<uint64_t, uint32_t>> map;
+    map.reserve(w.len);
+    uint32_t k = w.pos;
+    for (uint64_t t : w.tickets)
+      for (uint64_t pg : slot(t).pages) map.push_back({pg, k++});
     pool->run(map.size(), [&](size_t i) {
       uint8_t *src = h_stage + (size_t)map[i].second * MS_PAGE_BYTES;
       std::memcpy(host + map[i].first * MS_PAGE_BYTES, src, MS_PAGE_BYTES);
