@@ -67,18 +67,34 @@ def test_per_page_domains_host_and_device_lists(ms, key1, shape):
         assert np.array_equal(d2.cpu().numpy(), want)
 
 
-def test_server_requests_with_domains(ms, key1):
-    n = 512
+@pytest.mark.parametrize("n,lane,zc", [(512, None, False), (4096, None, False), (4096, 0, False),
+                                       (4096, None, True)])
+def test_server_requests_with_domains(ms, key1, n, lane, zc):
+    """Requests with their own domain words through the in-place lane (short
+    queue), through long in-place waves (thousands of pages queued at once),
+    staged (lane off) and in zero-copy mode."""
     plain = synth.page_bytes(94, 0, n)
     h = torch.from_numpy(plain.copy()).pin_memory()
-    pages = synth.scattered_slots(95, n, 400)
-    doms = np.repeat(np.array([7, 11, 13, 7], dtype=np.uint32), 100)
-    with ms.Context(key1, domain=5) as ctx, ms.Server(ctx, h, n) as srv:
-        ts = [srv.submit(ms.MS_ENCRYPT, pages[i:i + 4], domain=int(doms[i])) for i in range(0, 400, 4)]
-        for t in ts:
-            srv.wait(t)
+    m = 400 if n == 512 else 4000
+    pages = synth.scattered_slots(95, n, m)
+    doms = np.repeat(np.array([7, 11, 13, 7], dtype=np.uint32), m // 4)
+    mode = ms.MS_SERVE_ZERO_COPY if zc else ms.MS_SERVE_CONTINUOUS
+    n_req = m // 4
+    offsets = (np.arange(n_req + 1) * 4).astype(np.uint64)
+    ops = np.full(n_req, ms.MS_ENCRYPT, dtype=np.int32)
+    with ms.Context(key1, domain=5) as ctx, ms.Server(ctx, h, n, mode=mode, zero_copy_max_pages=lane) as srv:
+        if n == 512:   # one at a time from Python: short queues, the lane
+            ts = [srv.submit(ms.MS_ENCRYPT, pages[i:i + 4], domain=int(doms[i])) for i in range(0, m, 4)]
+            for t in ts:
+                srv.wait(t)
+        else:          # all at once from the replay: the queue outgrows the lane
+            srv.replay(np.zeros(n_req), ops, offsets, pages, domains=doms[::4].copy())
+        st = srv.stats()
     want = oracle_by_domain(key1, plain, pages.astype(np.uint64), pages.astype(np.uint64), doms)
     assert np.array_equal(h.numpy(), want)
+    assert (st["staged_waves"] == st["waves"]) if lane == 0 else (st["staged_waves"] == 0)
+    if n > 512 and lane is None and not zc:
+        assert st["waves"] > st["inplace_waves"]       # long in-place waves formed
 
 
 @pytest.mark.parametrize("window,batch", [(4, 1), (8, 1), (8, 4), (16, 9)])
