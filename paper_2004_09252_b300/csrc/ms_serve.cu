@@ -218,7 +218,7 @@ struct ms_server {
 
   Req &slot(uint64_t t) { return reqs[t % reqs.size()]; }
   void loop();
-  void take_inbox();
+  bool take_inbox(bool wait);
   bool form_wave(Wave &w);
   bool form_inplace(Wave &w, uint32_t max_pages);
   int issue(Wave &w);
@@ -242,14 +242,24 @@ void atomic_max(std::atomic<uint64_t> &a, uint64_t v) {
 // considered per wave.
 constexpr size_t kScanWindow = 4096;
 
-void ms_server::take_inbox() {
+// wait = false (a serving pass): leave the inbox for the next pass if a
+// submitter holds its lock, so that a submitting thread that is descheduled
+// inside its short critical section never holds up the server thread.
+// Returns false when it left the inbox so (the caller must not go idle).
+bool ms_server::take_inbox(bool wait) {
   {
-    std::lock_guard<std::mutex> lk(inmu);
-    if (inbox.empty()) return;
+    std::unique_lock<std::mutex> lk(inmu, std::defer_lock);
+    if (wait) {
+      lk.lock();
+    } else if (!lk.try_lock()) {
+      return false;
+    }
+    if (inbox.empty()) return true;
     inbox.swap(inbox_spare);  // the inbox keeps the spare's (empty) buffer
   }
   incoming.insert(incoming.end(), inbox_spare.begin(), inbox_spare.end());
   inbox_spare.clear();
+  return true;
 }
 
 bool ms_server::form_wave(Wave &w) {
@@ -429,7 +439,7 @@ void ms_server::complete(Wave &w) {
 
 void ms_server::fail_all(int code) {
   error.store(code);
-  take_inbox();  // a submission that saw no error under inmu is in the inbox by now
+  take_inbox(true);  // a submission that saw no error under inmu is in the inbox by now
   std::lock_guard<std::mutex> lk(qmu);
   for (auto *set : {&inflight, &inflight_inplace})
     for (Wave &w : *set)
@@ -486,8 +496,9 @@ void ms_server::loop() {
       it = inflight_inplace.erase(it);
       progress = true;
     }
-    take_inbox();
-    if (stop.load()) {
+    const bool stopping = stop.load();
+    const bool missed = !take_inbox(stopping);  // stopping: every request submitted so far must be seen
+    if (stopping) {
       const bool empty = incoming.empty();
       if (empty && inflight.empty() && inflight_inplace.empty()) break;
       if (!stop_deadline) stop_deadline = now_ns() + (uint64_t)ctx->cfg.timeout_ms * 1000000ull;
@@ -533,7 +544,7 @@ void ms_server::loop() {
       }
     }
     atomic_max(st_max_pass, now_ns() - t_pass);  // this pass's work, without its idle waits
-    if (progress) {
+    if (progress || missed) {  // missed: a submission is in the inbox, take it next pass
       idle_since = 0;
       continue;
     }
@@ -682,7 +693,7 @@ static int submit_internal(ms_server *s, int op, uint32_t domain, const uint64_t
       if (std::adjacent_find(tmp.begin(), tmp.end()) != tmp.end()) return MS_EINVAL;
     }
   }
-  std::lock_guard<std::mutex> lk(s->inmu);
+  std::unique_lock<std::mutex> lk(s->inmu);
   if (s->error.load()) return s->error.load();  // under inmu: fail_all drains the inbox after setting it
   if (s->stop.load()) return MS_ENOTINIT;
   const uint64_t t = s->next_ticket.load();
@@ -702,7 +713,8 @@ static int submit_internal(ms_server *s, int op, uint32_t domain, const uint64_t
   r.state.store(kQueued, std::memory_order_release);
   s->inbox.push_back(t);
   if (ticket) *ticket = t;
-  s->qcv.notify_one();
+  lk.unlock();
+  s->qcv.notify_one();  // after the unlock: the server thread wakes to a free lock
   return MS_OK;
 }
 
