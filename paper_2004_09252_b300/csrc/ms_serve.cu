@@ -195,6 +195,7 @@ struct ms_server {
   std::condition_variable qcv;       // with inmu: wakes an idle server thread
   std::vector<uint64_t> inbox;       // submitted tickets, in submission order (guarded by inmu)
   std::vector<uint64_t> inbox_spare; // the server thread's swap buffer for the inbox
+  uint64_t taken_upto = 0;           // next_ticket as of the last take of the inbox (server thread)
   std::mutex qmu;
   std::deque<uint64_t> incoming;     // server thread only
   std::atomic<uint64_t> next_ticket{0};
@@ -254,6 +255,7 @@ bool ms_server::take_inbox(bool wait) {
     } else if (!lk.try_lock()) {
       return false;
     }
+    taken_upto = next_ticket.load();  // every ticket below this is in `incoming` or beyond
     if (inbox.empty()) return true;
     inbox.swap(inbox_spare);  // the inbox keeps the spare's (empty) buffer
   }
@@ -550,8 +552,10 @@ void ms_server::loop() {
     }
     if (inflight.empty() && inflight_inplace.empty()) {
       // idle: watch the ticket counter for a while before blocking, so a
-      // request that arrives soon is picked up without a wake-up delay
-      const uint64_t seen = next_ticket.load(), t_idle = now_ns();
+      // request that arrives soon is picked up without a wake-up delay (a
+      // request submitted since the last take of the inbox ends the wait
+      // at once)
+      const uint64_t seen = taken_upto, t_idle = now_ns();
       while (next_ticket.load() == seen && !stop.load() && now_ns() - t_idle < idle_spin_ns) nap_ns(1000);
       if (next_ticket.load() == seen && !stop.load()) {
         std::unique_lock<std::mutex> lk(inmu);
