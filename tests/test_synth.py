@@ -1,5 +1,6 @@
 """The seeded input generators: counter form = sequential form, numpy = C, recipe shapes."""
 import numpy as np
+import pytest
 
 import synth
 
@@ -56,6 +57,30 @@ def test_serving_recipe():
     assert np.all(np.diff(arr) >= 0)
     assert abs(len(arr) / arr[-1] - 10000.0) / 10000.0 < 0.05
     for r in range(0, 5000, 97):
+        seg = pages[off[r]:off[r + 1]]
+        assert len(np.unique(seg)) == len(seg)
+
+
+@pytest.mark.parametrize("n_ws", [1 << 20, 4096, 70])
+def test_serving_duplicates_fixed_as_walked(n_ws):
+    """The duplicate fix-up finds its requests with one sort; the result is
+    the same as walking every multi-page request in order, and every
+    request's pages are distinct (small working sets force many repeats)."""
+    arr, ops, off, pages = synth.serving_workload(9, 3000, 80000.0, n_ws)
+    raw = (synth.splitmix64(9 ^ 0x3333, 0, int(off[-1])) % np.uint64(n_ws)).astype(np.int64)
+    walked = raw.copy()
+    for r in range(len(off) - 1):
+        seg = walked[off[r]:off[r + 1]]
+        if len(seg) > 1 and len(np.unique(seg)) != len(seg):
+            seen = set()
+            for i in range(len(seg)):
+                v = int(seg[i])
+                while v in seen:
+                    v = (v + 1) % n_ws
+                seen.add(v)
+                seg[i] = v
+    assert np.array_equal(pages, walked)
+    for r in range(len(off) - 1):
         seg = pages[off[r]:off[r + 1]]
         assert len(np.unique(seg)) == len(seg)
 
