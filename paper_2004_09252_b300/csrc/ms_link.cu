@@ -4,8 +4,8 @@
 // index); what differs is the launch shape.
 //
 // On B300 behind this host, SM-issued read-modify-write traffic to host
-// memory depends on how much of it is in flight, not on the access pattern
-// (measured with 64 threads per page, pages in random order):
+// memory depends first on how much of it is in flight (measured with 64
+// threads per page, pages in random order):
 //   - a grid of one thread per keystream block (tens of thousands of threads
 //     in flight): about 7.5 GB/s each way, whatever the CTA size;
 //   - 16 CTAs x 512 threads striding over the blocks, each thread loading its
